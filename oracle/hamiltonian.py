@@ -57,3 +57,56 @@ def dense_h(qmins, qmaxs, ns, mass, V, F_upper):
 def apply_h(H, psi):
     """H psi for a state of shape (S, *grid)."""
     return (H @ psi.reshape(-1)).reshape(psi.shape)
+
+
+def _derivative_kernel(qmin, qmax, n):
+    """First column of the circulant D = Phi^{-1} diag(i k) Phi:
+    d(m) = (1/n) sum_k i k_k exp(2 pi i k m / n), m = 0..n-1 (explicit sum)."""
+    k = _grid.wavenumbers(qmin, qmax, n)
+    d = np.empty(n, dtype=np.complex128)
+    kk = np.arange(n)
+    for m0 in range(0, n, 256):
+        m = np.arange(m0, min(n, m0 + 256))
+        ph = np.exp(2j * np.pi * ((np.outer(m, kk) % n) / n))
+        d[m0:m0 + len(m)] = (ph @ (1j * k)) / n
+    return d
+
+
+def _circulant_apply(d, x, adjoint=False):
+    """(D x)_j = sum_l d((j - l) mod n) x_l; adjoint: (D^H x)_j = sum_l conj(d((l - j) mod n)) x_l."""
+    n = len(d)
+    out = np.empty(n, dtype=np.complex128)
+    l = np.arange(n)
+    for j0 in range(0, n, 512):
+        j = np.arange(j0, min(n, j0 + 512))
+        if adjoint:
+            blk = np.conj(d[(l[None, :] - j[:, None]) % n])
+        else:
+            blk = d[(j[:, None] - l[None, :]) % n]
+        out[j0:j0 + len(j)] = blk @ x
+    return out
+
+
+def apply_h_matrix_free(qmin, qmax, n, mass, V, F_upper, psi):
+    """H psi on a 1-D grid without forming H (for grids too large for dense
+    matrices): A psi with A = p - i hbar F, p = -i hbar D, then
+    H psi = (1/2m) A^H (A psi) + V psi with A^H = p^H + (-i hbar F)^H taken
+    literally (conjugate transposes of the circulant D and of F)."""
+    V = np.asarray(V, dtype=np.float64)
+    S = V.shape[0]
+    Ff = coupling_full(F_upper, S)[0]          # (S, S, n)
+    d = _derivative_kernel(qmin, qmax, n)
+    psi = np.asarray(psi, dtype=np.complex128).reshape(S, n)
+    Apsi = np.empty_like(psi)
+    for s in range(S):
+        acc = -1j * HBAR * _circulant_apply(d, psi[s])
+        for t in range(S):
+            acc = acc - 1j * HBAR * Ff[s, t] * psi[t]
+        Apsi[s] = acc
+    out = np.empty_like(psi)
+    for s in range(S):
+        acc = np.conj(-1j * HBAR) * _circulant_apply(d, Apsi[s], adjoint=True)
+        for t in range(S):
+            acc = acc + np.conj(-1j * HBAR) * Ff[t, s] * Apsi[t]
+        out[s] = acc / (2.0 * mass) + V[s] * psi[s]
+    return out

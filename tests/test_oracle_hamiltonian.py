@@ -69,3 +69,13 @@ def test_adiabatic_hamiltonian_has_the_diabatic_spectrum():
     f2 = F[0, 0] ** 2 / (2 * m)
     Hbad -= np.diag(np.concatenate([f2, f2]))
     assert np.abs(np.linalg.eigvalsh(Hbad)[:16] - ed).max() > 1e-7
+
+
+def test_matrix_free_action_equals_dense_matrix():
+    n = 64
+    V, F = wl.random_adiabatic_fields(3, 1, (n,), seed=11)
+    psi = wl.random_psi(3, (n,), seed=12)
+    H = ham.dense_h([1.0], [9.0], [n], [5.0], V, F)
+    a = ham.apply_h(H, psi)
+    b = ham.apply_h_matrix_free(1.0, 9.0, n, 5.0, V, F, psi)
+    assert np.linalg.norm(a - b) < 1e-12 * np.linalg.norm(a)
