@@ -1,0 +1,221 @@
+/*
+ * qgeom.h -- C-ABI of the GB300 (sm_103a) library for composed implicit
+ * propagation of multi-surface nuclear wavepackets on Fourier grids in the
+ * adiabatic representation (Choi & Vanicek, arXiv:1902.04661).
+ *
+ * The method: the time-dependent Schroedinger equation (Eq. tdse) with the
+ * adiabatic molecular Hamiltonian (Eq. adiab_mol_ham)
+ *     H = 1/2 [p 1 - i hbar F(q)]^dagger . m^{-1} . [p 1 - i hbar F(q)] + V(q)
+ * is propagated by the trapezoidal rule (Eq. trap_rule) or the implicit
+ * midpoint method (Eq. imp_midpoint), each the product of an explicit Euler
+ * (Eq. exp_euler) and an implicit Euler (Eq. imp_euler) half step.  Every
+ * implicit half step solves (1 + i tau H) x = b, tau = dt / (2 hbar), with
+ * restarted GMRES started from the explicit-Euler guess (Sec. II B).  The
+ * elementary steps are composed recursively and symmetrically by the triple
+ * jump (Eq. triple_jump) or Suzuki's fractal (Eq. suzukis_fractal) to orders
+ * 2, 4, 6, 8 (Sec. II C).  H psi is evaluated by the dynamic Fourier method
+ * (Sec. II D): 4 D Fourier transforms per surface.
+ *
+ * Units: Hartree atomic units, hbar = 1.  Times in atomic units of time.
+ *
+ * Conventions shared by every entry point:
+ *  - Grid: dimension d has N_d points q_j = qmin_d + j dq_d, j = 0..N_d-1,
+ *    dq_d = (qmax_d - qmin_d) / N_d (periodic).  N_d must be a power of two,
+ *    8 <= N_d <= 8192.  Only D = 1 grids are accepted by this version.
+ *  - Wave numbers k_j = 2 pi / (N dq) (j for j < N/2, j - N otherwise).
+ *  - Inner product <a|b> = prod_d dq_d * sum_s sum_j conj(a_s(q_j)) b_s(q_j).
+ *  - A molecular state is S * prod(N_d) complex values (double2 = {re, im}),
+ *    surface-major: element (s, j) at index s * prod(N_d) + j, grid points in
+ *    C order.
+ *  - Adiabatic surfaces are ordered by ascending energy (0 = ground).
+ *  - V is S * prod(N_d) doubles (surface-major).  F is the upper triangle of
+ *    the real antisymmetric coupling matrices: D * S(S-1)/2 * prod(N_d)
+ *    doubles, dimension-major, pairs (i < j) in lexicographic order
+ *    (01, 02, 12 for S = 3); F_ji = -F_ij and F_ii = 0 are implied.
+ *  - Diabatic W is the upper triangle including the diagonal:
+ *    S(S+1)/2 * prod(N_d) doubles, pairs (i <= j) lexicographic
+ *    (00, 01, 11 for S = 2); dW is D * S(S+1)/2 * prod(N_d) doubles of
+ *    dW/dq_d.
+ *
+ * Ownership: the library owns every handle and the device workspaces behind
+ * it; the caller owns every buffer it passes.  A buffer flagged on_device is
+ * a device pointer of the current device and is read or written in stream
+ * order on the state's stream; a host buffer is copied synchronously.
+ *
+ * Errors: every call returns a qg_status and never throws across the ABI.
+ * A propagation that fails (GMRES not converged within the iteration cap)
+ * restores the state it was given and returns QG_ERR_NOT_CONVERGED with the
+ * statistics filled in.  Invalid handles or sizes return QG_ERR_INVALID_ARG
+ * before any device work.  CUDA errors return QG_ERR_CUDA
+ * (qg_last_error_string() gives the CUDA message).
+ */
+#ifndef QGEOM_H
+#define QGEOM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QG_OK = 0,
+  QG_ERR_INVALID_ARG = 1,
+  QG_ERR_NOT_CONVERGED = 2,
+  QG_ERR_CUDA = 3,
+  QG_ERR_OOM = 4,
+  QG_ERR_TIMEOUT = 5,
+  QG_ERR_UNSUPPORTED = 6
+} qg_status;
+
+/* Elementary second-order methods (Sec. II B). */
+enum { QG_TRAPEZOIDAL = 0,   /* U_impl(dt/2) U_expl(dt/2), Eq. (trap_rule)    */
+       QG_MIDPOINT = 1 };    /* U_expl(dt/2) U_impl(dt/2), Eq. (imp_midpoint) */
+/* Composition schemes (Sec. II C). */
+enum { QG_TRIPLE_JUMP = 0,   /* Eq. (triple_jump), M = 3, C = 3^(order/2-1)     */
+       QG_SUZUKI = 1 };      /* Eq. (suzukis_fractal), M = 5, C = 5^(order/2-1) */
+/* State precision. */
+enum { QG_C128 = 0 };
+
+typedef struct qg_grid* qg_grid_t;
+typedef struct qg_model* qg_model_t;
+typedef struct qg_state* qg_state_t;
+typedef struct qg_batch* qg_batch_t;
+
+/* Linear-solver options for the implicit half steps (Sec. II B).
+ * tol: stop when the GMRES residual estimate |g_{j+1}| <= tol * ||b||
+ *      (relative residual in the inner-product norm), default 1e-12.
+ * restart: Krylov dimension m of GMRES(m), 1..64, default 30.
+ * max_iters: cap on the total Arnoldi iterations of one implicit solve
+ *      (all restarts), default 400; exceeding it is QG_ERR_NOT_CONVERGED.
+ * reorth: 1 = classical Gram-Schmidt with one re-orthogonalisation pass
+ *      (CGS2, default), 0 = single pass.
+ * midpoint_epilogue: 0 = psi' = 2 chi - psi (default; equal to the explicit
+ *      half step up to the solver residual), 1 = psi' = chi - i tau H chi as
+ *      written in Eq. (imp_midpoint) (one more H psi per step).
+ * true_residual: 1 = recompute ||b - A x|| after convergence and restart if
+ *      it exceeds tol (one more H psi per solve); default 0. */
+typedef struct {
+  double tol;
+  int restart;
+  int max_iters;
+  int reorth;
+  int midpoint_epilogue;
+  int true_residual;
+} qg_solver_opts;
+
+/* Statistics of one propagate / step call (summed over all sub-steps). */
+typedef struct {
+  int64_t n_hpsi;          /* H psi evaluations                                */
+  int64_t n_krylov;        /* Arnoldi iterations (I summed over sub-steps)     */
+  int64_t n_substeps;      /* elementary steps taken (C per composed step)     */
+  int32_t max_krylov;      /* largest I of one implicit solve                  */
+  int32_t status;          /* qg_status of the call                            */
+  double max_residual;     /* largest final relative residual estimate         */
+  int64_t failed_step;     /* composed-step index that failed, or -1           */
+  int64_t n_ortho;         /* sum over Arnoldi iterations j of (j + 1): basis
+                              vectors orthogonalised against, per pass          */
+  int64_t n_update;        /* basis vectors summed into the solution           */
+  int64_t n_restart;       /* GMRES restarts and true-residual re-checks (one
+                              H psi each)                                       */
+} qg_step_stats;
+
+/* Fill opts with the defaults listed above. */
+void qg_default_solver_opts(qg_solver_opts* opts);
+
+/* Grid of D dimensions (Sec. II D; Sec. III uses D = 1, N = 2048 on
+ * [3.8, 47.0) a.u.).  N, qmin, qmax: arrays of D entries, qmax > qmin.
+ * Builds the FP64 twiddle and wave-number tables on the current device. */
+qg_status qg_create_grid(int D, const int* N, const double* qmin, const double* qmax,
+                         qg_grid_t* out);
+void qg_destroy_grid(qg_grid_t g);
+
+/* Adiabatic model from its fields (Eq. adiab_mol_ham): S surfaces (2..4),
+ * mass: D nuclear masses (electron masses), V and F in the layouts above.
+ * on_device: 1 = V, F are device pointers (copied device-to-device),
+ * 0 = host pointers.  The grid must outlive the model. */
+qg_status qg_create_model(qg_grid_t g, int S, const double* mass, const double* V,
+                          const double* F, int on_device, qg_model_t* out);
+
+/* Adiabatic model from a two-state diabatic matrix W(q) and its derivative
+ * (Sec. II E): V_{1,2} = Wbar +- sqrt((dW/2)^2 + W12^2) (Eq. pot_diab2adiab
+ * with the orthogonal matrix of Eq. ..._orthogonal_transformation) and the
+ * coupling of Eq. (nonadiab_c), computed on the device per grid point.  The
+ * paper labels the upper surface 1; this library stores surfaces ascending,
+ * so V[0] is the ground and F[0] = F_{ground,excited} = -F_12 (paper).
+ * S must be 2. */
+qg_status qg_create_model_diabatic(qg_grid_t g, int S, const double* mass, const double* W,
+                                   const double* dW, int on_device, qg_model_t* out);
+/* Copy the model's V and F (layouts above) to host (on_device = 0) or device
+ * buffers. */
+qg_status qg_model_fields(qg_model_t m, double* V, double* F, int on_device);
+void qg_destroy_model(qg_model_t m);
+
+/* Molecular wavepacket for a model (owns S * prod(N_d) complex128 values and
+ * the solver workspace).  precision must be QG_C128. */
+qg_status qg_create_state(qg_model_t m, int precision, qg_state_t* out);
+void qg_destroy_state(qg_state_t s);
+/* Stream (cudaStream_t) on which the state's work is ordered; NULL = the
+ * legacy default stream. */
+qg_status qg_state_set_stream(qg_state_t s, void* stream);
+qg_status qg_set_state(qg_state_t s, const void* psi, int on_device);
+qg_status qg_get_state(qg_state_t s, void* psi, int on_device);
+/* Gaussian wavepacket on one surface, zero on the others (Sec. III):
+ * psi(q) = prod_d exp(-(q_d - q0_d)^2 / (4 sigma0_d^2) + i p0_d (q_d - q0_d)),
+ * normalised on the grid.  q0, p0, sigma0: D entries each. */
+qg_status qg_set_gaussian(qg_state_t s, int surface, const double* q0, const double* p0,
+                          const double* sigma0);
+
+/* out = H psi (Eq. adiab_mol_ham by the dynamic Fourier method, Sec. II D);
+ * out: S * prod(N_d) complex128, host or device per on_device. */
+qg_status qg_apply_h(qg_state_t s, void* out, int on_device);
+
+/* One composed time step dt (Secs. II B, II C): method QG_TRAPEZOIDAL or
+ * QG_MIDPOINT, order 2/4/6/8, scheme QG_TRIPLE_JUMP or QG_SUZUKI.  opts may
+ * be NULL (defaults); stats may be NULL. */
+qg_status qg_step_implicit(qg_state_t s, int method, int order, int scheme, double dt,
+                           const qg_solver_opts* opts, qg_step_stats* stats);
+/* nsteps composed steps in one device launch. */
+qg_status qg_propagate(qg_state_t s, int method, int order, int scheme, double dt,
+                       int64_t nsteps, const qg_solver_opts* opts, qg_step_stats* stats);
+
+/* Observables (Sec. II A): norm ||psi||, energy <psi|H|psi>, populations
+ * P_s = ||psi_s||^2 (out: S doubles), overlap <a|b> (out: {re, im}).
+ * Results are written to host memory; the call synchronises the stream. */
+qg_status qg_norm(qg_state_t s, double* out);
+qg_status qg_energy(qg_state_t s, double* out);
+qg_status qg_population(qg_state_t s, double* out);
+qg_status qg_overlap(qg_state_t a, qg_state_t b, double* out);
+
+/* Batched form: nstates independent states (each with its own model and
+ * grid) propagated in ONE persistent launch; each CTA takes instances from
+ * an on-device work counter.  statuses / stats: per-instance outputs of
+ * nstates entries on the host (either may be NULL).  The stream of states[0]
+ * is used.  Returns QG_ERR_NOT_CONVERGED if any instance failed (those
+ * instances are restored; the others advance). */
+qg_status qg_batch_propagate(qg_state_t* states, int nstates, int method, int order, int scheme,
+                             double dt, int64_t nsteps, const qg_solver_opts* opts,
+                             int32_t* statuses, qg_step_stats* stats);
+
+/* Reusable batch: the device instance table, work counter and per-instance
+ * statistics for a fixed list of states, built once so that repeated
+ * qg_batch_run calls allocate nothing.  The states must outlive the batch
+ * and keep their models; the stream of states[0] is used. */
+qg_status qg_batch_create(qg_state_t* states, int nstates, qg_batch_t* out);
+/* Same semantics as qg_batch_propagate on the batch's states. */
+qg_status qg_batch_run(qg_batch_t b, int method, int order, int scheme, double dt, int64_t nsteps,
+                       const qg_solver_opts* opts, int32_t* statuses, qg_step_stats* stats);
+void qg_batch_destroy(qg_batch_t b);
+
+/* Human-readable name of a status; message of the last CUDA error seen by
+ * this thread. */
+const char* qg_status_string(qg_status st);
+const char* qg_last_error_string(void);
+/* Library version string. */
+const char* qg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QGEOM_H */

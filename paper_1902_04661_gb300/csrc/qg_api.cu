@@ -1,0 +1,605 @@
+// Host side of libqgeom: handles, FFT plans and tables, the C-ABI.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qg_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(const char* what, cudaError_t e) {
+  snprintf(g_err, sizeof(g_err), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+}
+
+#define QG_TRY(call)                               \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) {                       \
+      set_err(#call, e_);                          \
+      return e_ == cudaErrorMemoryAllocation ? QG_ERR_OOM : QG_ERR_CUDA; \
+    }                                              \
+  } while (0)
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2h(int v) {
+  int k = 0;
+  while ((1 << k) < v) ++k;
+  return k;
+}
+
+// Radix sequence for n = 2^k (k >= 3): as many radix-8 passes as possible,
+// the remainder as one or two radix-4 passes.
+FftPlan make_plan(int n) {
+  FftPlan p;
+  p.n = n;
+  p.npass = 0;
+  const int k = ilog2h(n);
+  int a = k / 3, rem = k % 3;
+  if (rem == 1) {
+    a -= 1;
+  }
+  for (int i = 0; i < a; ++i) p.radix[p.npass++] = 8;
+  if (rem == 2) p.radix[p.npass++] = 4;
+  if (rem == 1) {
+    p.radix[p.npass++] = 4;
+    p.radix[p.npass++] = 4;
+  }
+  return p;
+}
+
+// Frequency index held at position p after the decimation-in-frequency
+// passes radix[first..]: a block of length len splits into R sub-blocks of
+// length len/R; sub-block q holds the frequencies q + R f' where f' is the
+// frequency at the same position inside the sub-transform.
+void freq_positions(int len, const int* radix, int npass, std::vector<int>& f) {
+  f.assign(len, 0);
+  if (npass == 0 || len == 1) return;
+  const int R = radix[0];
+  const int m = len / R;
+  std::vector<int> sub;
+  freq_positions(m, radix + 1, npass - 1, sub);
+  for (int q = 0; q < R; ++q)
+    for (int pp = 0; pp < m; ++pp) f[q * m + pp] = q + R * sub[pp];
+}
+
+// exp(-2 pi i k / n) for k = 0..n-1.  cos/sin are evaluated in long double
+// on the first octant and mapped to the others by exact symmetries.
+void twiddles(int n, std::vector<double2>& tw) {
+  tw.resize(n);
+  std::vector<long double> c(n / 8 + 1), s(n / 8 + 1);
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int k = 0; k <= n / 8; ++k) {
+    const long double a = two_pi * (long double)k / (long double)n;
+    c[k] = cosl(a);
+    s[k] = sinl(a);
+  }
+  for (int k = 0; k < n; ++k) {
+    long double ck, sk;  // cos, sin of 2 pi k / n
+    int kk = k;
+    long double sgn_s = 1.0L;
+    if (kk > n / 2) {  // angle = 2 pi - angle(n - k)
+      kk = n - kk;
+      sgn_s = -1.0L;
+    }
+    long double cb, sb;
+    if (kk <= n / 8) {
+      cb = c[kk];
+      sb = s[kk];
+    } else if (kk <= n / 4) {
+      cb = s[n / 4 - kk];
+      sb = c[n / 4 - kk];
+    } else if (kk <= 3 * n / 8) {
+      cb = -s[kk - n / 4];
+      sb = c[kk - n / 4];
+    } else {
+      cb = -c[n / 2 - kk];
+      sb = s[n / 2 - kk];
+    }
+    ck = cb;
+    sk = sgn_s * sb;
+    tw[k] = make_double2((double)ck, (double)(-sk));
+  }
+}
+
+void default_opts(qg_solver_opts* o) {
+  o->tol = 1e-12;
+  o->restart = 30;
+  o->max_iters = 400;
+  o->reorth = 1;
+  o->midpoint_epilogue = 0;
+  o->true_residual = 0;
+}
+
+bool valid_opts(const qg_solver_opts& o) {
+  return o.tol > 0.0 && o.restart >= 1 && o.restart <= QG_MAX_RESTART && o.max_iters >= 1 &&
+         (o.reorth == 0 || o.reorth == 1) && (o.midpoint_epilogue == 0 || o.midpoint_epilogue == 1) &&
+         (o.true_residual == 0 || o.true_residual == 1);
+}
+
+// Composition fractions (Sec. II C): order 2 is the elementary step; each
+// recursion level maps the list L of order p to gamma_1 L, ..., gamma_M L
+// with the coefficients of Eq. (triple_jump) or Eq. (suzukis_fractal).
+bool make_schedule(int order, int scheme, std::vector<double>& fr) {
+  if (order < 2 || order > 8 || (order & 1)) return false;
+  if (scheme != QG_TRIPLE_JUMP && scheme != QG_SUZUKI) return false;
+  fr.assign(1, 1.0);
+  for (int p = 2; p < order; p += 2) {
+    std::vector<double> g;
+    if (scheme == QG_TRIPLE_JUMP) {
+      const double r = std::pow(2.0, 1.0 / (p + 1));
+      g = {1.0 / (2.0 - r), -r / (2.0 - r), 1.0 / (2.0 - r)};
+    } else {
+      const double r = std::pow(4.0, 1.0 / (p + 1));
+      const double a = 1.0 / (4.0 - r);
+      g = {a, a, -r / (4.0 - r), a, a};
+    }
+    std::vector<double> nx;
+    for (double gi : g)
+      for (double f : fr) nx.push_back(gi * f);
+    fr.swap(nx);
+  }
+  return (int)fr.size() <= QG_MAX_FRACTIONS;
+}
+
+InstDesc make_desc(const qg_state* s) {
+  const qg_model* m = s->m;
+  const qg_grid* g = m->g;
+  InstDesc d;
+  memset(&d, 0, sizeof(d));
+  d.n = g->n[0];
+  d.S = m->S;
+  d.npass = g->plan[0].npass;
+  for (int i = 0; i < QG_MAX_PASSES; ++i) d.radix[i] = g->plan[0].radix[i];
+  d.h2m = 1.0 / (2.0 * m->mass[0]);
+  d.dq = g->dq[0];
+  d.tw = g->d_tw[0];
+  d.kd = g->d_kd[0];
+  d.V = m->d_V;
+  d.F = m->d_F;
+  d.psi = s->d_psi;
+  d.work = s->d_work;
+  d.restart_cap = s->restart_cap;
+  return d;
+}
+
+}  // namespace
+
+static qg_status upload_desc(qg_state_t s) {
+  InstDesc d = make_desc(s);
+  QG_TRY(cudaMemcpyAsync(s->d_inst, &d, sizeof(d), cudaMemcpyHostToDevice, s->stream));
+  return QG_OK;
+}
+
+extern "C" {
+
+void qg_default_solver_opts(qg_solver_opts* opts) {
+  if (opts) default_opts(opts);
+}
+
+const char* qg_version(void) { return "qgeom 0.1 (sm_103a)"; }
+
+const char* qg_last_error_string(void) { return g_err; }
+
+const char* qg_status_string(qg_status st) {
+  switch (st) {
+    case QG_OK: return "ok";
+    case QG_ERR_INVALID_ARG: return "invalid argument";
+    case QG_ERR_NOT_CONVERGED: return "implicit solve did not converge";
+    case QG_ERR_CUDA: return "CUDA error";
+    case QG_ERR_OOM: return "out of device memory";
+    case QG_ERR_TIMEOUT: return "timeout";
+    case QG_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+qg_status qg_create_grid(int D, const int* N, const double* qmin, const double* qmax, qg_grid_t* out) {
+  if (!out || !N || !qmin || !qmax) return QG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (D < 1 || D > QG_MAX_D) return D == 2 ? QG_ERR_UNSUPPORTED : QG_ERR_INVALID_ARG;
+  for (int d = 0; d < D; ++d) {
+    if (!is_pow2(N[d]) || N[d] < QG_MIN_N || N[d] > QG_MAX_N) return QG_ERR_INVALID_ARG;
+    if (!(qmax[d] > qmin[d]) || !std::isfinite(qmin[d]) || !std::isfinite(qmax[d])) return QG_ERR_INVALID_ARG;
+  }
+  qg_grid* g = new (std::nothrow) qg_grid;
+  if (!g) return QG_ERR_OOM;
+  memset(g, 0, sizeof(*g));
+  g->D = D;
+  g->ntot = 1;
+  cudaGetDevice(&g->device);
+  for (int d = 0; d < D; ++d) {
+    const int n = N[d];
+    g->n[d] = n;
+    g->qmin[d] = qmin[d];
+    g->qmax[d] = qmax[d];
+    g->dq[d] = (qmax[d] - qmin[d]) / n;
+    g->ntot *= n;
+    g->plan[d] = make_plan(n);
+    std::vector<double2> tw;
+    twiddles(n, tw);
+    std::vector<int> f;
+    freq_positions(n, g->plan[d].radix, g->plan[d].npass, f);
+    std::vector<double> kd(n);
+    const double k0 = 2.0 * M_PI / (n * g->dq[d]);
+    for (int p = 0; p < n; ++p) {
+      const int ff = f[p] < n / 2 ? f[p] : f[p] - n;
+      kd[p] = k0 * ff / n;
+    }
+    cudaError_t e = cudaMalloc(&g->d_tw[d], sizeof(double2) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_kd[d], sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_tw[d], tw.data(), sizeof(double2) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_kd[d], kd.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      set_err("qg_create_grid", e);
+      qg_destroy_grid(g);
+      return e == cudaErrorMemoryAllocation ? QG_ERR_OOM : QG_ERR_CUDA;
+    }
+  }
+  *out = g;
+  return QG_OK;
+}
+
+void qg_destroy_grid(qg_grid_t g) {
+  if (!g) return;
+  for (int d = 0; d < 2; ++d) {
+    if (g->d_tw[d]) cudaFree(g->d_tw[d]);
+    if (g->d_kd[d]) cudaFree(g->d_kd[d]);
+  }
+  delete g;
+}
+
+static qg_status alloc_model(qg_grid_t g, int S, const double* mass, qg_model** out) {
+  *out = nullptr;
+  if (!g || !mass || S < 2 || S > QG_MAX_S) return QG_ERR_INVALID_ARG;
+  for (int d = 0; d < g->D; ++d)
+    if (!(mass[d] > 0.0) || !std::isfinite(mass[d])) return QG_ERR_INVALID_ARG;
+  qg_model* m = new (std::nothrow) qg_model;
+  if (!m) return QG_ERR_OOM;
+  memset(m, 0, sizeof(*m));
+  m->g = g;
+  m->S = S;
+  for (int d = 0; d < g->D; ++d) m->mass[d] = mass[d];
+  const size_t nv = (size_t)S * g->ntot;
+  const size_t nf = (size_t)g->D * (S * (S - 1) / 2) * g->ntot;
+  cudaError_t e = cudaMalloc(&m->d_V, sizeof(double) * nv);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_F, sizeof(double) * nf);
+  if (e != cudaSuccess) {
+    set_err("qg_create_model", e);
+    qg_destroy_model(m);
+    return e == cudaErrorMemoryAllocation ? QG_ERR_OOM : QG_ERR_CUDA;
+  }
+  *out = m;
+  return QG_OK;
+}
+
+qg_status qg_create_model(qg_grid_t g, int S, const double* mass, const double* V, const double* F, int on_device,
+                          qg_model_t* out) {
+  if (!out || !V || !F) return QG_ERR_INVALID_ARG;
+  qg_model* m;
+  qg_status st = alloc_model(g, S, mass, &m);
+  if (st != QG_OK) return st;
+  const size_t nv = (size_t)S * g->ntot;
+  const size_t nf = (size_t)g->D * (S * (S - 1) / 2) * g->ntot;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaMemcpy(m->d_V, V, sizeof(double) * nv, k);
+  if (e == cudaSuccess) e = cudaMemcpy(m->d_F, F, sizeof(double) * nf, k);
+  if (e != cudaSuccess) {
+    set_err("qg_create_model", e);
+    qg_destroy_model(m);
+    return QG_ERR_CUDA;
+  }
+  *out = m;
+  return QG_OK;
+}
+
+qg_status qg_create_model_diabatic(qg_grid_t g, int S, const double* mass, const double* W, const double* dW,
+                                   int on_device, qg_model_t* out) {
+  if (!out || !W || !dW) return QG_ERR_INVALID_ARG;
+  if (S != 2) return QG_ERR_UNSUPPORTED;
+  qg_model* m;
+  qg_status st = alloc_model(g, S, mass, &m);
+  if (st != QG_OK) return st;
+  const int n = g->ntot;
+  double *dWd = nullptr, *ddW = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    e = cudaMalloc(&dWd, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&ddW, sizeof(double) * 3 * n);
+    if (e == cudaSuccess) e = cudaMemcpy(dWd, W, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ddW, dW, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess)
+    e = qg_launch_fields2(on_device ? W : dWd, on_device ? dW : ddW, n, m->d_V, m->d_F, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (dWd) cudaFree(dWd);
+  if (ddW) cudaFree(ddW);
+  if (e != cudaSuccess) {
+    set_err("qg_create_model_diabatic", e);
+    qg_destroy_model(m);
+    return QG_ERR_CUDA;
+  }
+  *out = m;
+  return QG_OK;
+}
+
+qg_status qg_model_fields(qg_model_t m, double* V, double* F, int on_device) {
+  if (!m) return QG_ERR_INVALID_ARG;
+  const size_t nv = (size_t)m->S * m->g->ntot;
+  const size_t nf = (size_t)m->g->D * (m->S * (m->S - 1) / 2) * m->g->ntot;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (V) QG_TRY(cudaMemcpy(V, m->d_V, sizeof(double) * nv, k));
+  if (F) QG_TRY(cudaMemcpy(F, m->d_F, sizeof(double) * nf, k));
+  return QG_OK;
+}
+
+void qg_destroy_model(qg_model_t m) {
+  if (!m) return;
+  if (m->d_V) cudaFree(m->d_V);
+  if (m->d_F) cudaFree(m->d_F);
+  delete m;
+}
+
+qg_status qg_create_state(qg_model_t m, int precision, qg_state_t* out) {
+  if (!out || !m) return QG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (precision != QG_C128) return QG_ERR_UNSUPPORTED;
+  qg_state* s = new (std::nothrow) qg_state;
+  if (!s) return QG_ERR_OOM;
+  memset(s, 0, sizeof(*s));
+  s->m = m;
+  s->restart_cap = QG_MAX_RESTART;
+  s->stream = 0;
+  const size_t len = (size_t)m->S * m->g->ntot;
+  cudaError_t e = cudaMalloc(&s->d_psi, sizeof(double2) * len);
+  if (e == cudaSuccess) e = cudaMemset(s->d_psi, 0, sizeof(double2) * len);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_work, sizeof(double2) * len * (size_t)(s->restart_cap + 5));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_stats, sizeof(qg_step_stats));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_scalars, sizeof(double) * 64);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_inst, sizeof(InstDesc));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, sizeof(int));
+  if (e != cudaSuccess) {
+    set_err("qg_create_state", e);
+    qg_destroy_state(s);
+    return e == cudaErrorMemoryAllocation ? QG_ERR_OOM : QG_ERR_CUDA;
+  }
+  qg_status st = upload_desc(s);
+  if (st == QG_OK) {
+    cudaError_t e2 = cudaStreamSynchronize(s->stream);
+    if (e2 != cudaSuccess) {
+      set_err("qg_create_state", e2);
+      st = QG_ERR_CUDA;
+    }
+  }
+  if (st != QG_OK) {
+    qg_destroy_state(s);
+    return st;
+  }
+  *out = s;
+  return QG_OK;
+}
+
+void qg_destroy_state(qg_state_t s) {
+  if (!s) return;
+  if (s->d_psi) cudaFree(s->d_psi);
+  if (s->d_work) cudaFree(s->d_work);
+  if (s->d_stats) cudaFree(s->d_stats);
+  if (s->d_scalars) cudaFree(s->d_scalars);
+  if (s->d_inst) cudaFree(s->d_inst);
+  if (s->d_counter) cudaFree(s->d_counter);
+  delete s;
+}
+
+qg_status qg_state_set_stream(qg_state_t s, void* stream) {
+  if (!s) return QG_ERR_INVALID_ARG;
+  s->stream = (cudaStream_t)stream;
+  return QG_OK;
+}
+
+qg_status qg_set_state(qg_state_t s, const void* psi, int on_device) {
+  if (!s || !psi) return QG_ERR_INVALID_ARG;
+  const size_t bytes = sizeof(double2) * (size_t)s->m->S * s->m->g->ntot;
+  QG_TRY(cudaMemcpyAsync(s->d_psi, psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         s->stream));
+  if (!on_device) QG_TRY(cudaStreamSynchronize(s->stream));
+  return QG_OK;
+}
+
+qg_status qg_get_state(qg_state_t s, void* psi, int on_device) {
+  if (!s || !psi) return QG_ERR_INVALID_ARG;
+  const size_t bytes = sizeof(double2) * (size_t)s->m->S * s->m->g->ntot;
+  QG_TRY(cudaMemcpyAsync(psi, s->d_psi, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         s->stream));
+  if (!on_device) QG_TRY(cudaStreamSynchronize(s->stream));
+  return QG_OK;
+}
+
+qg_status qg_set_gaussian(qg_state_t s, int surface, const double* q0, const double* p0, const double* sigma0) {
+  if (!s || !q0 || !p0 || !sigma0) return QG_ERR_INVALID_ARG;
+  const qg_grid* g = s->m->g;
+  if (surface < 0 || surface >= s->m->S) return QG_ERR_INVALID_ARG;
+  if (!(sigma0[0] > 0.0) || !std::isfinite(q0[0]) || !std::isfinite(p0[0])) return QG_ERR_INVALID_ARG;
+  QG_TRY(qg_launch_gaussian(s->d_psi, g->n[0], s->m->S, surface, g->qmin[0], g->dq[0], q0[0], p0[0], sigma0[0],
+                            s->stream));
+  return QG_OK;
+}
+
+qg_status qg_apply_h(qg_state_t s, void* out, int on_device) {
+  if (!s || !out) return QG_ERR_INVALID_ARG;
+  const qg_grid* g = s->m->g;
+  const size_t len = (size_t)s->m->S * g->ntot;
+  double2* dst = on_device ? (double2*)out : s->d_work + 1 * len;  // B slot as staging
+  QG_TRY(qg_launch_apply_h(s->d_inst, dst, g->n[0], s->m->S, s->stream));
+  if (!on_device) {
+    QG_TRY(cudaMemcpyAsync(out, dst, sizeof(double2) * len, cudaMemcpyDeviceToHost, s->stream));
+    QG_TRY(cudaStreamSynchronize(s->stream));
+  }
+  return QG_OK;
+}
+
+static qg_status build_plan(int method, int order, int scheme, double dt, int64_t nsteps, const qg_solver_opts* opts,
+                            StepPlan* P) {
+  qg_solver_opts o;
+  default_opts(&o);
+  if (opts) o = *opts;
+  if (!valid_opts(o)) return QG_ERR_INVALID_ARG;
+  if (method != QG_TRAPEZOIDAL && method != QG_MIDPOINT) return QG_ERR_INVALID_ARG;
+  if (!std::isfinite(dt) || nsteps < 0) return QG_ERR_INVALID_ARG;
+  std::vector<double> fr;
+  if (!make_schedule(order, scheme, fr)) return QG_ERR_INVALID_ARG;
+  memset(P, 0, sizeof(*P));
+  P->method = method;
+  P->nfrac = (int)fr.size();
+  for (size_t i = 0; i < fr.size(); ++i) P->frac[i] = fr[i];
+  P->dt = dt;
+  P->nsteps = nsteps;
+  P->tol = o.tol;
+  P->restart = o.restart;
+  P->max_iters = o.max_iters;
+  P->reorth = o.reorth;
+  P->mid_epi = o.midpoint_epilogue;
+  P->true_res = o.true_residual;
+  return QG_OK;
+}
+
+qg_status qg_propagate(qg_state_t s, int method, int order, int scheme, double dt, int64_t nsteps,
+                       const qg_solver_opts* opts, qg_step_stats* stats) {
+  if (!s) return QG_ERR_INVALID_ARG;
+  StepPlan P;
+  qg_status st = build_plan(method, order, scheme, dt, nsteps, opts, &P);
+  if (st != QG_OK) return st;
+  const qg_grid* g = s->m->g;
+  QG_TRY(qg_launch_propagate(s->d_inst, 1, P, s->d_counter, s->d_stats, g->n[0], s->m->S, s->stream));
+  qg_step_stats h;
+  QG_TRY(cudaMemcpyAsync(&h, s->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  QG_TRY(cudaStreamSynchronize(s->stream));
+  if (stats) *stats = h;
+  return (qg_status)h.status;
+}
+
+qg_status qg_step_implicit(qg_state_t s, int method, int order, int scheme, double dt, const qg_solver_opts* opts,
+                           qg_step_stats* stats) {
+  return qg_propagate(s, method, order, scheme, dt, 1, opts, stats);
+}
+
+qg_status qg_batch_create(qg_state_t* states, int nstates, qg_batch_t* out) {
+  if (!out || !states || nstates < 1) return QG_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < nstates; ++i)
+    if (!states[i]) return QG_ERR_INVALID_ARG;
+  qg_batch* b = new (std::nothrow) qg_batch;
+  if (!b) return QG_ERR_OOM;
+  b->n = nstates;
+  b->stream = states[0]->stream;
+  b->max_n = 0;
+  b->max_S = 0;
+  b->d_desc = nullptr;
+  b->d_stats = nullptr;
+  b->d_counter = nullptr;
+  b->h_stats = nullptr;
+  std::vector<InstDesc> descs(nstates);
+  for (int i = 0; i < nstates; ++i) {
+    descs[i] = make_desc(states[i]);
+    if (descs[i].n > b->max_n) b->max_n = descs[i].n;
+    if (descs[i].S > b->max_S) b->max_S = descs[i].S;
+  }
+  cudaError_t e = cudaMalloc(&b->d_desc, sizeof(InstDesc) * nstates);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_stats, sizeof(qg_step_stats) * nstates);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_stats, sizeof(qg_step_stats) * nstates);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, descs.data(), sizeof(InstDesc) * nstates, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    set_err("qg_batch_create", e);
+    qg_batch_destroy(b);
+    return e == cudaErrorMemoryAllocation ? QG_ERR_OOM : QG_ERR_CUDA;
+  }
+  *out = b;
+  return QG_OK;
+}
+
+void qg_batch_destroy(qg_batch_t b) {
+  if (!b) return;
+  if (b->d_desc) cudaFree(b->d_desc);
+  if (b->d_stats) cudaFree(b->d_stats);
+  if (b->d_counter) cudaFree(b->d_counter);
+  if (b->h_stats) cudaFreeHost(b->h_stats);
+  delete b;
+}
+
+qg_status qg_batch_run(qg_batch_t b, int method, int order, int scheme, double dt, int64_t nsteps,
+                       const qg_solver_opts* opts, int32_t* statuses, qg_step_stats* stats) {
+  if (!b) return QG_ERR_INVALID_ARG;
+  StepPlan P;
+  qg_status st = build_plan(method, order, scheme, dt, nsteps, opts, &P);
+  if (st != QG_OK) return st;
+  QG_TRY(qg_launch_propagate(b->d_desc, b->n, P, b->d_counter, b->d_stats, b->max_n, b->max_S, b->stream));
+  QG_TRY(cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(qg_step_stats) * b->n, cudaMemcpyDeviceToHost, b->stream));
+  QG_TRY(cudaStreamSynchronize(b->stream));
+  qg_status ret = QG_OK;
+  for (int i = 0; i < b->n; ++i) {
+    if (statuses) statuses[i] = b->h_stats[i].status;
+    if (stats) stats[i] = b->h_stats[i];
+    if (b->h_stats[i].status != QG_OK) ret = QG_ERR_NOT_CONVERGED;
+  }
+  return ret;
+}
+
+qg_status qg_batch_propagate(qg_state_t* states, int nstates, int method, int order, int scheme, double dt,
+                             int64_t nsteps, const qg_solver_opts* opts, int32_t* statuses, qg_step_stats* stats) {
+  qg_batch_t b = nullptr;
+  qg_status st = qg_batch_create(states, nstates, &b);
+  if (st != QG_OK) return st;
+  st = qg_batch_run(b, method, order, scheme, dt, nsteps, opts, statuses, stats);
+  qg_batch_destroy(b);
+  return st;
+}
+
+qg_status qg_norm(qg_state_t s, double* out) {
+  if (!s || !out) return QG_ERR_INVALID_ARG;
+  double pop[QG_MAX_S];
+  qg_status st = qg_population(s, pop);
+  if (st != QG_OK) return st;
+  double t = 0.0;
+  for (int i = 0; i < s->m->S; ++i) t += pop[i];
+  *out = std::sqrt(t);
+  return QG_OK;
+}
+
+qg_status qg_population(qg_state_t s, double* out) {
+  if (!s || !out) return QG_ERR_INVALID_ARG;
+  const qg_grid* g = s->m->g;
+  QG_TRY(qg_launch_populations(s->d_psi, g->n[0], s->m->S, g->dq[0], s->d_scalars, s->stream));
+  QG_TRY(cudaMemcpyAsync(out, s->d_scalars, sizeof(double) * s->m->S, cudaMemcpyDeviceToHost, s->stream));
+  QG_TRY(cudaStreamSynchronize(s->stream));
+  return QG_OK;
+}
+
+qg_status qg_energy(qg_state_t s, double* out) {
+  if (!s || !out) return QG_ERR_INVALID_ARG;
+  const qg_grid* g = s->m->g;
+  QG_TRY(qg_launch_energy(s->d_inst, s->d_scalars, g->n[0], s->m->S, s->stream));
+  double v[2];
+  QG_TRY(cudaMemcpyAsync(v, s->d_scalars, sizeof(v), cudaMemcpyDeviceToHost, s->stream));
+  QG_TRY(cudaStreamSynchronize(s->stream));
+  *out = v[0];
+  return QG_OK;
+}
+
+qg_status qg_overlap(qg_state_t a, qg_state_t b, double* out) {
+  if (!a || !b || !out) return QG_ERR_INVALID_ARG;
+  if (a->m->S != b->m->S || a->m->g->ntot != b->m->g->ntot) return QG_ERR_INVALID_ARG;
+  const size_t len = (size_t)a->m->S * a->m->g->ntot;
+  QG_TRY(cudaStreamSynchronize(b->stream));
+  QG_TRY(qg_launch_overlap(a->d_psi, b->d_psi, (int)len, a->m->g->dq[0], a->d_scalars, a->stream));
+  QG_TRY(cudaMemcpyAsync(out, a->d_scalars, sizeof(double) * 2, cudaMemcpyDeviceToHost, a->stream));
+  QG_TRY(cudaStreamSynchronize(a->stream));
+  return QG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// Internal declarations shared by the host API and the kernels of libqgeom.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qgeom.h"
+
+#define QG_MAX_S 4
+#define QG_MAX_D 1
+#define QG_MAX_RESTART 64
+#define QG_MAX_PASSES 8
+#define QG_MAX_FRACTIONS 128
+#define QG_MIN_N 8
+#define QG_MAX_N 8192
+#define QG_THREADS 256
+
+// Radix plan of one power-of-two FFT length.  Passes run in the listed order
+// for the forward (decimation-in-frequency) transform and in reverse order
+// for the inverse (decimation-in-time) transform.
+struct FftPlan {
+  int n;
+  int npass;
+  int radix[QG_MAX_PASSES];
+};
+
+struct qg_grid {
+  int D;
+  int n[2];
+  double qmin[2], qmax[2], dq[2];
+  int ntot;
+  FftPlan plan[2];
+  double2* d_tw[2];  // tw[k] = exp(-2 pi i k / n), k = 0..n-1
+  double* d_kd[2];   // k of the frequency held at digit-reversed position p, divided by n
+  int device;
+};
+
+struct qg_model {
+  qg_grid* g;
+  int S;
+  double mass[2];
+  double* d_V;  // S * ntot
+  double* d_F;  // D * S(S-1)/2 * ntot (upper triangle)
+};
+
+struct InstDesc;
+
+struct qg_state {
+  qg_model* m;
+  InstDesc* d_inst;         // this state's instance descriptor (device)
+  int* d_counter;           // work counter of the persistent kernel (device)
+  double2* d_psi;    // S * ntot
+  double2* d_work;   // (restart_cap + 5) vectors of S * ntot
+  int restart_cap;
+  cudaStream_t stream;
+  qg_step_stats* d_stats;   // one record
+  double* d_scalars;        // small device scratch for observables
+};
+
+// Everything one CTA needs to work on one instance (a state with its model
+// and grid), in device memory.
+struct InstDesc {
+  int n;          // grid points
+  int S;          // surfaces
+  int npass;
+  int radix[QG_MAX_PASSES];
+  double h2m;     // hbar^2 / (2 m)
+  double dq;
+  const double2* tw;
+  const double* kd;
+  const double* V;
+  const double* F;
+  double2* psi;
+  double2* work;  // U, B, X, P0, then basis V_0..V_m (each S * n)
+  int restart_cap;
+};
+
+// Parameters of one propagate launch (passed by value).
+struct StepPlan {
+  int method;
+  int nfrac;
+  double dt;
+  long long nsteps;
+  double tol;
+  int restart;
+  int max_iters;
+  int reorth;
+  int mid_epi;
+  int true_res;
+  double frac[QG_MAX_FRACTIONS];
+};
+
+struct qg_batch {
+  int n;
+  int max_n, max_S;
+  cudaStream_t stream;
+  InstDesc* d_desc;
+  qg_step_stats* d_stats;
+  int* d_counter;
+  qg_step_stats* h_stats;   // pinned
+};
+
+// Launch wrappers (qg_kernels.cu).
+size_t qg_smem_bytes(int max_n, int max_S, int restart);
+cudaError_t qg_launch_propagate(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
+                                qg_step_stats* d_stats, int max_n, int max_S, cudaStream_t st);
+cudaError_t qg_launch_apply_h(const InstDesc* d_inst, double2* d_out, int n, int S, cudaStream_t st);
+cudaError_t qg_launch_energy(const InstDesc* d_inst, double* d_out, int n, int S, cudaStream_t st);
+cudaError_t qg_launch_populations(const double2* d_psi, int n, int S, double dq, double* d_out, cudaStream_t st);
+cudaError_t qg_launch_overlap(const double2* d_a, const double2* d_b, int len, double dq, double* d_out,
+                              cudaStream_t st);
+cudaError_t qg_launch_gaussian(double2* d_psi, int n, int S, int surface, double qmin, double dq, double q0,
+                               double p0, double sigma0, cudaStream_t st);
+cudaError_t qg_launch_fields2(const double* d_W, const double* d_dW, int n, double* d_V, double* d_F,
+                              cudaStream_t st);

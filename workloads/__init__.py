@@ -14,3 +14,4 @@ from .constants import (AU_TIME_PER_FS, NAI_REDUCED_MASS, NAI_QMIN, NAI_QMAX,
                         PHI_Q0, PHI_P0)
 from .nai_like import nai_like_diabatic, nai_like_params, initial_gaussian_params
 from .random_inputs import random_psi, random_adiabatic_fields
+from .avoided_crossing import avoided_crossing_model
