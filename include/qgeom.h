@@ -207,6 +207,36 @@ qg_status qg_batch_run(qg_batch_t b, int method, int order, int scheme, double d
                        const qg_solver_opts* opts, int32_t* statuses, qg_step_stats* stats);
 void qg_batch_destroy(qg_batch_t b);
 
+/* Propagation without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that are not allowed to allocate GPU
+ * memory -- for example a plug-in running inside a host application whose
+ * own allocator owns the device memory, or code that must not allocate after
+ * start-up.  It propagates one state like qg_propagate but takes every input
+ * as a raw pointer (no handles), and keeps all of its scratch (FFT tables,
+ * GMRES workspace, statistics) in one fixed device array of about 3 MB that
+ * lives in the library for the life of the process on every GPU that loads
+ * it.  It calls no cudaMalloc / cudaFree and no allocating library routine.
+ *   N: grid points (power of two, 8..8192) on [qmin, qmax); S: 2..4
+ *   surfaces, with S * N <= 8192; mass: nuclear mass (electron masses);
+ *   V (S*N doubles) and F (S(S-1)/2 * N doubles): device pointers in the
+ *   layouts above; psi: device pointer to S*N complex128, read and
+ *   overwritten in place; method / order / scheme / dt / nsteps as in
+ *   qg_propagate; opts may be NULL (defaults with restart 16; a restart
+ *   above 16 is rejected); stats (host) may be NULL; stream: cudaStream_t
+ *   (NULL = legacy default stream).  The call returns after the stream has
+ *   finished the propagation.
+ * The first call on a device looks up the array's device address and builds
+ * the FFT tables; make that first call before any stream capture.  Sizes
+ * beyond the capacity return QG_ERR_INVALID_ARG with a message in
+ * qg_last_error_string().  Every call shares the one array, whose contents
+ * persist between calls (nothing in it needs to start at zero: each call
+ * rewrites what it reads); calls that overlap on the GPU, on any stream or
+ * thread, race and corrupt each other's results. */
+qg_status qg_propagate_noalloc(int N, double qmin, double qmax, int S, double mass, const double* V,
+                               const double* F, void* psi, int method, int order, int scheme, double dt,
+                               int64_t nsteps, const qg_solver_opts* opts, qg_step_stats* stats,
+                               void* stream);
+
 /* Human-readable name of a status; message of the last CUDA error seen by
  * this thread. */
 const char* qg_status_string(qg_status st);

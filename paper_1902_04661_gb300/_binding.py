@@ -35,7 +35,7 @@ EXPORTED = [
     "qg_create_model_diabatic", "qg_model_fields", "qg_destroy_model", "qg_create_state",
     "qg_destroy_state", "qg_state_set_stream", "qg_set_state", "qg_get_state", "qg_set_gaussian",
     "qg_apply_h", "qg_step_implicit", "qg_propagate", "qg_norm", "qg_energy", "qg_population",
-    "qg_overlap", "qg_batch_propagate", "qg_batch_create", "qg_batch_run", "qg_batch_destroy", "qg_status_string", "qg_last_error_string", "qg_version",
+    "qg_overlap", "qg_batch_propagate", "qg_batch_create", "qg_batch_run", "qg_batch_destroy", "qg_propagate_noalloc", "qg_status_string", "qg_last_error_string", "qg_version",
 ]
 
 
@@ -105,6 +105,8 @@ def lib():
             "qg_batch_run": (I, [P, I, I, I, D, ctypes.c_int64, ctypes.POINTER(SolverOpts),
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(StepStats)]),
             "qg_batch_destroy": (V, [P]),
+            "qg_propagate_noalloc": (I, [I, D, D, I, D, P, P, P, I, I, I, D, ctypes.c_int64,
+                                         ctypes.POINTER(SolverOpts), ctypes.POINTER(StepStats), P]),
             "qg_status_string": (ctypes.c_char_p, [I]),
             "qg_last_error_string": (ctypes.c_char_p, []),
             "qg_version": (ctypes.c_char_p, []),

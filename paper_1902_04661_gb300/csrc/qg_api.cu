@@ -602,4 +602,92 @@ qg_status qg_overlap(qg_state_t a, qg_state_t b, double* out) {
   return QG_OK;
 }
 
+// Composition fractions into a fixed array (no heap): same recursion as
+// make_schedule.  Returns the count, or 0 for an invalid order / scheme.
+static int schedule_fixed(int order, int scheme, double* out) {
+  if (order < 2 || order > 8 || (order & 1)) return 0;
+  if (scheme != QG_TRIPLE_JUMP && scheme != QG_SUZUKI) return 0;
+  double tmp[QG_MAX_FRACTIONS];
+  int cnt = 1;
+  out[0] = 1.0;
+  for (int p = 2; p < order; p += 2) {
+    double g[5];
+    int M;
+    if (scheme == QG_TRIPLE_JUMP) {
+      const double r = std::pow(2.0, 1.0 / (p + 1));
+      g[0] = g[2] = 1.0 / (2.0 - r);
+      g[1] = -r / (2.0 - r);
+      M = 3;
+    } else {
+      const double r = std::pow(4.0, 1.0 / (p + 1));
+      g[0] = g[1] = g[3] = g[4] = 1.0 / (4.0 - r);
+      g[2] = -r / (4.0 - r);
+      M = 5;
+    }
+    if (cnt * M > QG_MAX_FRACTIONS) return 0;
+    int k = 0;
+    for (int a = 0; a < M; ++a)
+      for (int b = 0; b < cnt; ++b) tmp[k++] = g[a] * out[b];
+    for (int b = 0; b < k; ++b) out[b] = tmp[b];
+    cnt = k;
+  }
+  return cnt;
+}
+
+qg_status qg_propagate_noalloc(int N, double qmin, double qmax, int S, double mass, const double* V, const double* F,
+                               void* psi, int method, int order, int scheme, double dt, int64_t nsteps,
+                               const qg_solver_opts* opts, qg_step_stats* stats, void* stream) {
+  if (!V || !F || !psi) {
+    snprintf(g_err, sizeof(g_err), "qg_propagate_noalloc: V, F and psi must be device pointers");
+    return QG_ERR_INVALID_ARG;
+  }
+  if (!is_pow2(N) || N < QG_MIN_N || N > QG_NA_MAX_N || S < 2 || S > QG_MAX_S || (int64_t)S * N > QG_NA_MAX_LEN) {
+    snprintf(g_err, sizeof(g_err),
+             "qg_propagate_noalloc: N = %d, S = %d outside the fixed scratch capacity "
+             "(N a power of two in [%d, %d], 2 <= S <= %d, S*N <= %d)",
+             N, S, QG_MIN_N, QG_NA_MAX_N, QG_MAX_S, QG_NA_MAX_LEN);
+    return QG_ERR_INVALID_ARG;
+  }
+  if (!(qmax > qmin) || !std::isfinite(qmin) || !std::isfinite(qmax) || !(mass > 0.0) || !std::isfinite(mass) ||
+      !std::isfinite(dt) || nsteps < 0 || (method != QG_TRAPEZOIDAL && method != QG_MIDPOINT)) {
+    snprintf(g_err, sizeof(g_err), "qg_propagate_noalloc: invalid grid, mass, method or step");
+    return QG_ERR_INVALID_ARG;
+  }
+  qg_solver_opts o;
+  default_opts(&o);
+  o.restart = QG_NA_MAX_RESTART;
+  if (opts) o = *opts;
+  if (!valid_opts(o) || o.restart > QG_NA_MAX_RESTART) {
+    snprintf(g_err, sizeof(g_err), "qg_propagate_noalloc: invalid solver options (restart must be <= %d)",
+             QG_NA_MAX_RESTART);
+    return QG_ERR_INVALID_ARG;
+  }
+  StepPlan P;
+  memset(&P, 0, sizeof(P));
+  P.nfrac = schedule_fixed(order, scheme, P.frac);
+  if (P.nfrac == 0) {
+    snprintf(g_err, sizeof(g_err), "qg_propagate_noalloc: invalid order or scheme");
+    return QG_ERR_INVALID_ARG;
+  }
+  P.method = method;
+  P.dt = dt;
+  P.nsteps = nsteps;
+  P.tol = o.tol;
+  P.restart = o.restart;
+  P.max_iters = o.max_iters;
+  P.reorth = o.reorth;
+  P.mid_epi = o.midpoint_epilogue;
+  P.true_res = o.true_residual;
+  const FftPlan plan = make_plan(N);
+  qg_step_stats h;
+  memset(&h, 0, sizeof(h));
+  cudaError_t e = qg_noalloc_launch(N, qmin, qmax, S, mass, V, F, (double2*)psi, plan, P, &h, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    set_err("qg_propagate_noalloc", e);
+    return QG_ERR_CUDA;
+  }
+  if (stats) *stats = h;
+  return (qg_status)h.status;
+}
+
 }  // extern "C"

@@ -14,6 +14,10 @@
 #define QG_MIN_N 8
 #define QG_MAX_N 8192
 #define QG_THREADS 256
+// Capacity of the no-allocation entry point (qg_propagate_noalloc).
+#define QG_NA_MAX_LEN 8192
+#define QG_NA_MAX_N 8192
+#define QG_NA_MAX_RESTART 16
 
 // Radix plan of one power-of-two FFT length.  Passes run in the listed order
 // for the forward (decimation-in-frequency) transform and in reverse order
@@ -111,5 +115,8 @@ cudaError_t qg_launch_overlap(const double2* d_a, const double2* d_b, int len, d
                               cudaStream_t st);
 cudaError_t qg_launch_gaussian(double2* d_psi, int n, int S, int surface, double qmin, double dq, double q0,
                                double p0, double sigma0, cudaStream_t st);
+cudaError_t qg_noalloc_launch(int n, double qmin, double qmax, int S, double mass, const double* V, const double* F,
+                              double2* psi, const FftPlan& plan, const StepPlan& P, qg_step_stats* host_stats,
+                              cudaStream_t st);
 cudaError_t qg_launch_fields2(const double* d_W, const double* d_dW, int n, double* d_V, double* d_F,
                               cudaStream_t st);
