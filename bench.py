@@ -36,16 +36,21 @@ WORKLOAD = dict(name="nai_like_n2048_s2_midpoint_suzuki", N=2048, S=2, method=1,
 FS = 41.341373335182
 
 
-def _flops_per_launch(stats, N, S, reorth=True):
+def _flops_per_launch(stats, N, S, reorth=True, mixed=False):
     """Algorithmic FP64 flops of the stats' work (complex FFT = 5 n log2 n):
     H psi: 4 S FFTs of length N plus (4 S^2 + 10 S) N pointwise; Arnoldi:
     16 S N per basis vector and Gram-Schmidt pass, 6 S N per iteration for the
-    norm and scaling; solution update 8 S N per basis vector."""
+    norm and scaling; solution update 8 S N per basis vector.  In the mixed
+    form the Krylov work is complex64 and only the FP64 H psi (residuals,
+    right-hand sides) and the refinement update (8 S N) count."""
     hpsi = 4 * S * 5 * N * math.log2(N) + (4 * S * S + 10 * S) * N
     ortho = (2 if reorth else 1) * 16 * S * N
     tot = 0.0
     for s in stats:
-        tot += s["n_hpsi"] * hpsi + s["n_ortho"] * ortho + s["n_krylov"] * 6 * S * N + s["n_update"] * 8 * S * N
+        if mixed:
+            tot += s["n_hpsi"] * hpsi + s["n_outer"] * 8 * S * N
+        else:
+            tot += s["n_hpsi"] * hpsi + s["n_ortho"] * ortho + s["n_krylov"] * 6 * S * N + s["n_update"] * 8 * S * N
     return tot
 
 
@@ -130,7 +135,7 @@ def fp64_peak_tflops(sm_mhz=None):
     return 152 * 4 * mhz * 1e6 / 1e12
 
 
-def _setup_batch(qg, wl, B, rank, stream):
+def _setup_batch(qg, wl, B, rank, stream, precision=0):
     N = WORKLOAD["N"]
     grid = qg.Grid([N], [wl.NAI_QMIN], [wl.NAI_QMAX])
     q = grid.points()
@@ -138,7 +143,7 @@ def _setup_batch(qg, wl, B, rank, stream):
     model = qg.Model(grid, 2, [wl.NAI_REDUCED_MASS], W=W, dW=dW)
     states = []
     for i in range(B):
-        st = qg.State(model, stream=stream)
+        st = qg.State(model, precision=precision, stream=stream)
         q0, p0, s0 = wl.initial_gaussian_params(rank * B + i)
         st.set_gaussian(1, [q0], [p0], [s0])
         states.append(st)
@@ -163,7 +168,8 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     B = args.batch or sms
     stream = torch.cuda.current_stream()
-    grid, model, states = _setup_batch(qg, wl, B, rank, stream.cuda_stream)
+    prec = qg.QG_C64_MIXED if args.precision == "mixed" else qg.QG_C128
+    grid, model, states = _setup_batch(qg, wl, B, rank, stream.cuda_stream, prec)
     batch = qg.Batch(states)
     opts = qg.default_solver_opts(tol=WORKLOAD["tol"], restart=WORKLOAD["restart"])
     dt = WORKLOAD["dt_fs"] * FS
@@ -197,7 +203,7 @@ def run_ours(args):
     steps_done = B * args.steps
     value = steps_done * world / (t_ms / 1e3)
     hpsi_rate = n_hpsi * N * world / (t_ms / 1e3)
-    flops = _flops_per_launch(flat, N, S) / args.steps
+    flops = _flops_per_launch(flat, N, S, mixed=(args.precision == "mixed")) / args.steps
     abytes = _bytes_per_launch(flat, N, S) / args.steps
     avg_launch_s = (t_ms / args.steps) / 1e3
     clocks = clk.summary()
@@ -237,17 +243,21 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "wavepacket-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == qg.QG_C128 else "c64 inner / f64 residual",
             "data": "synthetic (seeded NaI-like model and Gaussians)",
             "config": {"workload": WORKLOAD["name"], "N": N, "S": S, "wavepackets_per_gpu": B,
                        "method": "implicit midpoint" if m == 1 else "trapezoidal",
                        "order": o, "scheme": "suzuki" if sc == 1 else "triple_jump",
                        "dt_fs": WORKLOAD["dt_fs"], "gmres_tol": WORKLOAD["tol"], "restart": WORKLOAD["restart"],
+                       "precision": args.precision,
                        "l2": "working set %.0f MB > L2 (129 MB): no flush needed" %
                              (B * (WORKLOAD["restart"] + 6) * len_state * 16 / 1e6)},
             "hpsi_grid_point_applications_per_s": hpsi_rate,
             "substeps_per_s": n_sub * world / (t_ms / 1e3),
             "krylov_iters_per_substep": sum(s["n_krylov"] for s in flat) / max(1, n_sub),
+            "fp64_hpsi_per_substep": n_hpsi / max(1, n_sub),
+            "c64_hpsi_per_substep": sum(s["n_hpsi32"] for s in flat) / max(1, n_sub),
             "hbm_frac_if_streamed": abytes / avg_launch_s / 1e9 / mp.get("hbm_gbs", 6695.2),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
@@ -352,6 +362,8 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="wavepackets per GPU (default: one per SM)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="fp64: every Krylov iteration in FP64; mixed: complex64 inner solves, FP64 refinement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -74,8 +74,13 @@ enum { QG_TRAPEZOIDAL = 0,   /* U_impl(dt/2) U_expl(dt/2), Eq. (trap_rule)    */
 /* Composition schemes (Sec. II C). */
 enum { QG_TRIPLE_JUMP = 0,   /* Eq. (triple_jump), M = 3, C = 3^(order/2-1)     */
        QG_SUZUKI = 1 };      /* Eq. (suzukis_fractal), M = 5, C = 5^(order/2-1) */
-/* State precision. */
-enum { QG_C128 = 0 };
+/* State precision: the state is always stored in complex128.  QG_C128 solves
+ * every implicit step in FP64.  QG_C64_MIXED runs the Krylov iterations in
+ * complex64 and refines in FP64: r = b - (1 + i tau H) x is evaluated in FP64,
+ * (1 + i tau H) d = r is solved in complex64 GMRES to inner_tol, x += d, until
+ * ||r|| <= tol ||b|| (FP64 residual), so the result meets the same tolerance.
+ * Compositions, the state update and the observables stay FP64. */
+enum { QG_C128 = 0, QG_C64_MIXED = 1 };
 
 typedef struct qg_grid* qg_grid_t;
 typedef struct qg_model* qg_model_t;
@@ -94,7 +99,11 @@ typedef struct qg_batch* qg_batch_t;
  *      half step up to the solver residual), 1 = psi' = chi - i tau H chi as
  *      written in Eq. (imp_midpoint) (one more H psi per step).
  * true_residual: 1 = recompute ||b - A x|| after convergence and restart if
- *      it exceeds tol (one more H psi per solve); default 0. */
+ *      it exceeds tol (one more H psi per solve); default 0.
+ * inner_tol: QG_C64_MIXED only -- relative tolerance of each complex64 inner
+ *      solve, default 1e-6.
+ * max_outer: QG_C64_MIXED only -- cap on FP64 refinement steps per implicit
+ *      solve, default 10; exceeding it is QG_ERR_NOT_CONVERGED. */
 typedef struct {
   double tol;
   int restart;
@@ -102,6 +111,8 @@ typedef struct {
   int reorth;
   int midpoint_epilogue;
   int true_residual;
+  double inner_tol;
+  int max_outer;
 } qg_solver_opts;
 
 /* Statistics of one propagate / step call (summed over all sub-steps). */
@@ -118,6 +129,8 @@ typedef struct {
   int64_t n_update;        /* basis vectors summed into the solution           */
   int64_t n_restart;       /* GMRES restarts and true-residual re-checks (one
                               H psi each)                                       */
+  int64_t n_hpsi32;        /* complex64 H psi evaluations (QG_C64_MIXED)       */
+  int64_t n_outer;         /* FP64 refinement steps (QG_C64_MIXED)             */
 } qg_step_stats;
 
 /* Fill opts with the defaults listed above. */
@@ -152,7 +165,7 @@ qg_status qg_model_fields(qg_model_t m, double* V, double* F, int on_device);
 void qg_destroy_model(qg_model_t m);
 
 /* Molecular wavepacket for a model (owns S * prod(N_d) complex128 values and
- * the solver workspace).  precision must be QG_C128. */
+ * the solver workspace).  precision: QG_C128 or QG_C64_MIXED. */
 qg_status qg_create_state(qg_model_t m, int precision, qg_state_t* out);
 void qg_destroy_state(qg_state_t s);
 /* Stream (cudaStream_t) on which the state's work is ordered; NULL = the

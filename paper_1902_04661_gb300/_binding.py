@@ -28,6 +28,7 @@ QG_MIDPOINT = 1
 QG_TRIPLE_JUMP = 0
 QG_SUZUKI = 1
 QG_C128 = 0
+QG_C64_MIXED = 1
 
 # Every symbol declared in include/qgeom.h.
 EXPORTED = [
@@ -51,14 +52,15 @@ class QgError(RuntimeError):
 
 class SolverOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
-                ("reorth", ctypes.c_int), ("midpoint_epilogue", ctypes.c_int), ("true_residual", ctypes.c_int)]
+                ("reorth", ctypes.c_int), ("midpoint_epilogue", ctypes.c_int), ("true_residual", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
     _fields_ = [("n_hpsi", ctypes.c_int64), ("n_krylov", ctypes.c_int64), ("n_substeps", ctypes.c_int64),
                 ("max_krylov", ctypes.c_int32), ("status", ctypes.c_int32), ("max_residual", ctypes.c_double),
                 ("failed_step", ctypes.c_int64), ("n_ortho", ctypes.c_int64), ("n_update", ctypes.c_int64),
-                ("n_restart", ctypes.c_int64)]
+                ("n_restart", ctypes.c_int64), ("n_hpsi32", ctypes.c_int64), ("n_outer", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

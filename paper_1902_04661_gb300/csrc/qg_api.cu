@@ -115,12 +115,15 @@ void default_opts(qg_solver_opts* o) {
   o->reorth = 1;
   o->midpoint_epilogue = 0;
   o->true_residual = 0;
+  o->inner_tol = 1e-6;
+  o->max_outer = 10;
 }
 
 bool valid_opts(const qg_solver_opts& o) {
   return o.tol > 0.0 && o.restart >= 1 && o.restart <= QG_MAX_RESTART && o.max_iters >= 1 &&
          (o.reorth == 0 || o.reorth == 1) && (o.midpoint_epilogue == 0 || o.midpoint_epilogue == 1) &&
-         (o.true_residual == 0 || o.true_residual == 1);
+         (o.true_residual == 0 || o.true_residual == 1) && o.inner_tol > 0.0 && o.inner_tol < 1.0 &&
+         o.max_outer >= 1 && o.max_outer <= 1000;
 }
 
 // Composition fractions (Sec. II C): order 2 is the elementary step; each
@@ -166,6 +169,12 @@ InstDesc make_desc(const qg_state* s) {
   d.psi = s->d_psi;
   d.work = s->d_work;
   d.restart_cap = s->restart_cap;
+  d.precision = s->precision;
+  d.tw32 = g->d_tw32[0];
+  d.kd32 = g->d_kd32[0];
+  d.V32 = m->d_V32;
+  d.F32 = m->d_F32;
+  d.work32 = s->d_work32;
   return d;
 }
 
@@ -232,10 +241,20 @@ qg_status qg_create_grid(int D, const int* N, const double* qmin, const double* 
       const int ff = f[p] < n / 2 ? f[p] : f[p] - n;
       kd[p] = k0 * ff / n;
     }
+    std::vector<float2> tw32(n);
+    std::vector<float> kd32(n);
+    for (int p = 0; p < n; ++p) {
+      tw32[p] = make_float2((float)tw[p].x, (float)tw[p].y);
+      kd32[p] = (float)kd[p];
+    }
     cudaError_t e = cudaMalloc(&g->d_tw[d], sizeof(double2) * n);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_kd[d], sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_tw32[d], sizeof(float2) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_kd32[d], sizeof(float) * n);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_tw[d], tw.data(), sizeof(double2) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_kd[d], kd.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_tw32[d], tw32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_kd32[d], kd32.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       set_err("qg_create_grid", e);
       qg_destroy_grid(g);
@@ -251,8 +270,20 @@ void qg_destroy_grid(qg_grid_t g) {
   for (int d = 0; d < 2; ++d) {
     if (g->d_tw[d]) cudaFree(g->d_tw[d]);
     if (g->d_kd[d]) cudaFree(g->d_kd[d]);
+    if (g->d_tw32[d]) cudaFree(g->d_tw32[d]);
+    if (g->d_kd32[d]) cudaFree(g->d_kd32[d]);
   }
   delete g;
+}
+
+// FP32 copies of the fields for the mixed-precision inner solves.
+static cudaError_t finish_model(qg_model* m) {
+  const size_t nv = (size_t)m->S * m->g->ntot;
+  const size_t nf = (size_t)m->g->D * (m->S * (m->S - 1) / 2) * m->g->ntot;
+  cudaError_t e = qg_launch_to_f32(m->d_V, m->d_V32, nv, 0);
+  if (e == cudaSuccess) e = qg_launch_to_f32(m->d_F, m->d_F32, nf, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e;
 }
 
 static qg_status alloc_model(qg_grid_t g, int S, const double* mass, qg_model** out) {
@@ -270,6 +301,8 @@ static qg_status alloc_model(qg_grid_t g, int S, const double* mass, qg_model** 
   const size_t nf = (size_t)g->D * (S * (S - 1) / 2) * g->ntot;
   cudaError_t e = cudaMalloc(&m->d_V, sizeof(double) * nv);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_F, sizeof(double) * nf);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_V32, sizeof(float) * nv);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_F32, sizeof(float) * nf);
   if (e != cudaSuccess) {
     set_err("qg_create_model", e);
     qg_destroy_model(m);
@@ -290,6 +323,7 @@ qg_status qg_create_model(qg_grid_t g, int S, const double* mass, const double* 
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   cudaError_t e = cudaMemcpy(m->d_V, V, sizeof(double) * nv, k);
   if (e == cudaSuccess) e = cudaMemcpy(m->d_F, F, sizeof(double) * nf, k);
+  if (e == cudaSuccess) e = finish_model(m);
   if (e != cudaSuccess) {
     set_err("qg_create_model", e);
     qg_destroy_model(m);
@@ -318,6 +352,7 @@ qg_status qg_create_model_diabatic(qg_grid_t g, int S, const double* mass, const
   if (e == cudaSuccess)
     e = qg_launch_fields2(on_device ? W : dWd, on_device ? dW : ddW, n, m->d_V, m->d_F, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = finish_model(m);
   if (dWd) cudaFree(dWd);
   if (ddW) cudaFree(ddW);
   if (e != cudaSuccess) {
@@ -343,23 +378,28 @@ void qg_destroy_model(qg_model_t m) {
   if (!m) return;
   if (m->d_V) cudaFree(m->d_V);
   if (m->d_F) cudaFree(m->d_F);
+  if (m->d_V32) cudaFree(m->d_V32);
+  if (m->d_F32) cudaFree(m->d_F32);
   delete m;
 }
 
 qg_status qg_create_state(qg_model_t m, int precision, qg_state_t* out) {
   if (!out || !m) return QG_ERR_INVALID_ARG;
   *out = nullptr;
-  if (precision != QG_C128) return QG_ERR_UNSUPPORTED;
+  if (precision != QG_C128 && precision != QG_C64_MIXED) return QG_ERR_INVALID_ARG;
   qg_state* s = new (std::nothrow) qg_state;
   if (!s) return QG_ERR_OOM;
   memset(s, 0, sizeof(*s));
   s->m = m;
   s->restart_cap = QG_MAX_RESTART;
+  s->precision = precision;
   s->stream = 0;
   const size_t len = (size_t)m->S * m->g->ntot;
   cudaError_t e = cudaMalloc(&s->d_psi, sizeof(double2) * len);
   if (e == cudaSuccess) e = cudaMemset(s->d_psi, 0, sizeof(double2) * len);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_work, sizeof(double2) * len * (size_t)(s->restart_cap + 5));
+  if (e == cudaSuccess && precision == QG_C64_MIXED)
+    e = cudaMalloc(&s->d_work32, sizeof(float2) * len * (size_t)(s->restart_cap + 4));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_stats, sizeof(qg_step_stats));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_scalars, sizeof(double) * 64);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_inst, sizeof(InstDesc));
@@ -389,6 +429,7 @@ void qg_destroy_state(qg_state_t s) {
   if (!s) return;
   if (s->d_psi) cudaFree(s->d_psi);
   if (s->d_work) cudaFree(s->d_work);
+  if (s->d_work32) cudaFree(s->d_work32);
   if (s->d_stats) cudaFree(s->d_stats);
   if (s->d_scalars) cudaFree(s->d_scalars);
   if (s->d_inst) cudaFree(s->d_inst);
@@ -465,6 +506,8 @@ static qg_status build_plan(int method, int order, int scheme, double dt, int64_
   P->reorth = o.reorth;
   P->mid_epi = o.midpoint_epilogue;
   P->true_res = o.true_residual;
+  P->inner_tol = o.inner_tol;
+  P->max_outer = o.max_outer;
   return QG_OK;
 }
 
@@ -678,6 +721,8 @@ qg_status qg_propagate_noalloc(int N, double qmin, double qmax, int S, double ma
   P.reorth = o.reorth;
   P.mid_epi = o.midpoint_epilogue;
   P.true_res = o.true_residual;
+  P.inner_tol = o.inner_tol;
+  P.max_outer = o.max_outer;
   const FftPlan plan = make_plan(N);
   qg_step_stats h;
   memset(&h, 0, sizeof(h));

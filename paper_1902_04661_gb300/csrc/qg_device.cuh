@@ -1,5 +1,7 @@
 // Device building blocks: complex arithmetic, deterministic CTA reductions,
-// the shared-memory FFT and the fused Hamiltonian action (Sec. II D-E).
+// the shared-memory FFT and the fused Hamiltonian action (Sec. II D-E),
+// templated on the real type R (double for the FP64 path, float for the
+// inner iterations of the mixed-precision form).
 //
 // Every CTA works on one instance.  All loops are bounded; nothing waits on
 // another CTA.
@@ -12,43 +14,64 @@ namespace qg {
 constexpr int kThreads = QG_THREADS;
 constexpr int kWarps = QG_THREADS / 32;
 
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+template <typename R>
+struct Cx;
+template <>
+struct Cx<double> {
+  using T = double2;
+};
+template <>
+struct Cx<float> {
+  using T = float2;
+};
+
+template <typename C>
+__device__ __forceinline__ C cmk(decltype(C::x) a, decltype(C::x) b) {
+  C c;
+  c.x = a;
+  c.y = b;
+  return c;
+}
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
 // a * b
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  return cmk<C>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 // a * conj(b)
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+template <typename C>
+__device__ __forceinline__ C cmulc(C a, C b) {
+  return cmk<C>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
 }
-// conj(a) * b
-__device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
-}
-__device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+template <typename C, typename R>
+__device__ __forceinline__ C cscale(R s, C a) { return cmk<C>(s * a.x, s * a.y); }
 // a + s * b (s real)
-__device__ __forceinline__ double2 caxpy_r(double s, double2 b, double2 a) {
-  return make_double2(fma(s, b.x, a.x), fma(s, b.y, a.y));
-}
+template <typename C, typename R>
+__device__ __forceinline__ C caxpy_r(R s, C b, C a) { return cmk<C>(fma(s, b.x, a.x), fma(s, b.y, a.y)); }
 // a + c * b (c complex)
-__device__ __forceinline__ double2 caxpy(double2 c, double2 b, double2 a) {
-  return make_double2(fma(c.x, b.x, fma(-c.y, b.y, a.x)), fma(c.x, b.y, fma(c.y, b.x, a.y)));
+template <typename C>
+__device__ __forceinline__ C caxpy(C c, C b, C a) {
+  return cmk<C>(fma(c.x, b.x, fma(-c.y, b.y, a.x)), fma(c.x, b.y, fma(c.y, b.x, a.y)));
 }
 // a - c * b (c complex)
-__device__ __forceinline__ double2 cnaxpy(double2 c, double2 b, double2 a) {
-  return make_double2(fma(-c.x, b.x, fma(c.y, b.y, a.x)), fma(-c.x, b.y, fma(-c.y, b.x, a.y)));
+template <typename C>
+__device__ __forceinline__ C cnaxpy(C c, C b, C a) {
+  return cmk<C>(fma(-c.x, b.x, fma(c.y, b.y, a.x)), fma(-c.x, b.y, fma(-c.y, b.x, a.y)));
 }
-__device__ __forceinline__ double2 mul_i(double2 a) { return make_double2(-a.y, a.x); }
+template <typename C>
+__device__ __forceinline__ C mul_i(C a) { return cmk<C>(-a.y, a.x); }
 
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 
 // ---------------------------------------------------------------------------
-// Deterministic CTA-wide sums of K doubles per thread.  The xor-butterfly
+// Deterministic CTA-wide sums of K values per thread.  The xor-butterfly
 // leaves bitwise identical sums in every lane; warps are then added in a
 // fixed order.  Result in out[0..K) (shared), visible after return.
-template <int K>
-__device__ __forceinline__ void cta_sum(double (&v)[K], double* red, double* out) {
+template <int K, typename R>
+__device__ __forceinline__ void cta_sum(R (&v)[K], R* red, R* out) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
 #pragma unroll
@@ -61,7 +84,7 @@ __device__ __forceinline__ void cta_sum(double (&v)[K], double* red, double* out
   }
   __syncthreads();
   if (threadIdx.x < K) {
-    double s = 0.0;
+    R s = 0;
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) s += red[ww * K + threadIdx.x];
     out[threadIdx.x] = s;
@@ -70,10 +93,11 @@ __device__ __forceinline__ void cta_sum(double (&v)[K], double* red, double* out
 }
 
 // sum_i |x_i|^2 over len elements (plain sum, no grid weight)
-__device__ __forceinline__ double cta_norm2(const double2* x, int len, double* red, double* out) {
-  double v[1] = {0.0};
+template <typename C, typename R>
+__device__ __forceinline__ R cta_norm2(const C* x, int len, R* red, R* out) {
+  R v[1] = {0};
   for (int i = threadIdx.x; i < len; i += kThreads) {
-    double2 a = x[i];
+    C a = x[i];
     v[0] = fma(a.x, a.x, fma(a.y, a.y, v[0]));
   }
   cta_sum<1>(v, red, out);
@@ -83,17 +107,17 @@ __device__ __forceinline__ double cta_norm2(const double2* x, int len, double* r
 // ---------------------------------------------------------------------------
 // Small DFTs in registers.  Forward uses w = exp(-2 pi i / R), inverse its
 // conjugate; no scaling.
-template <bool INV>
-__device__ __forceinline__ void dft2(double2& a, double2& b) {
-  double2 t = a;
+template <bool INV, typename C>
+__device__ __forceinline__ void dft2(C& a, C& b) {
+  C t = a;
   a = cadd(t, b);
   b = csub(t, b);
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft4(double2& x0, double2& x1, double2& x2, double2& x3) {
-  double2 a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
-  double2 id = mul_i(d);
+template <bool INV, typename C>
+__device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
+  C a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
+  C id = mul_i(d);
   x0 = cadd(a, c);
   x2 = csub(a, c);
   if (!INV) {
@@ -105,22 +129,23 @@ __device__ __forceinline__ void dft4(double2& x0, double2& x1, double2& x2, doub
   }
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft8(double2 (&x)[8]) {
-  const double r2 = 0.70710678118654752440;
-  double2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
-  double2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+template <bool INV, typename C>
+__device__ __forceinline__ void dft8(C (&x)[8]) {
+  using R = decltype(C::x);
+  const R r2 = (R)0.70710678118654752440;
+  C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
   dft4<INV>(e0, e1, e2, e3);
   dft4<INV>(o0, o1, o2, o3);
-  double2 t1, t2, t3;
+  C t1, t2, t3;
   if (!INV) {
-    t1 = make_double2((o1.x + o1.y) * r2, (o1.y - o1.x) * r2);     // (1 - i)/sqrt2
-    t2 = make_double2(o2.y, -o2.x);                                 // -i
-    t3 = make_double2((o3.y - o3.x) * r2, -(o3.x + o3.y) * r2);    // (-1 - i)/sqrt2
+    t1 = cmk<C>((o1.x + o1.y) * r2, (o1.y - o1.x) * r2);     // (1 - i)/sqrt2
+    t2 = cmk<C>(o2.y, -o2.x);                                 // -i
+    t3 = cmk<C>((o3.y - o3.x) * r2, -(o3.x + o3.y) * r2);    // (-1 - i)/sqrt2
   } else {
-    t1 = make_double2((o1.x - o1.y) * r2, (o1.x + o1.y) * r2);     // (1 + i)/sqrt2
-    t2 = make_double2(-o2.y, o2.x);                                 // i
-    t3 = make_double2(-(o3.x + o3.y) * r2, (o3.x - o3.y) * r2);    // (-1 + i)/sqrt2
+    t1 = cmk<C>((o1.x - o1.y) * r2, (o1.x + o1.y) * r2);     // (1 + i)/sqrt2
+    t2 = cmk<C>(-o2.y, o2.x);                                 // i
+    t3 = cmk<C>(-(o3.x + o3.y) * r2, (o3.x - o3.y) * r2);    // (-1 + i)/sqrt2
   }
   x[0] = cadd(e0, o0);
   x[4] = csub(e0, o0);
@@ -132,85 +157,99 @@ __device__ __forceinline__ void dft8(double2 (&x)[8]) {
   x[7] = csub(e3, t3);
 }
 
-template <int R, bool INV>
-__device__ __forceinline__ void dft(double2 (&x)[R]) {
-  if constexpr (R == 2) {
+template <int RD, bool INV, typename C>
+__device__ __forceinline__ void dft(C (&x)[RD]) {
+  if constexpr (RD == 2) {
     dft2<INV>(x[0], x[1]);
-  } else if constexpr (R == 4) {
+  } else if constexpr (RD == 4) {
     dft4<INV>(x[0], x[1], x[2], x[3]);
   } else {
     dft8<INV>(x);
   }
 }
 
-// One radix-R pass over nb vectors of length n in shared memory, in place.
-// Block length L, m = L / R.  Forward (decimation in frequency): DFT over the
-// R elements j + r m of a block, then multiply by w_L^{j r}.  Inverse
+// Operands of one H psi evaluation in one precision.
+template <typename R>
+struct HOp {
+  using C = typename Cx<R>::T;
+  int n, S, npass;
+  int radix[QG_MAX_PASSES];
+  R h2m;
+  const C* tw;   // exp(-2 pi i k / n)
+  const R* kd;   // k at digit-reversed positions, divided by n
+  const R* V;
+  const R* F;
+  C* U;          // scratch vector (S * n)
+};
+
+// One radix-RD pass over nb vectors of length n in shared memory, in place.
+// Block length L, m = L / RD.  Forward (decimation in frequency): DFT over the
+// RD elements j + r m of a block, then multiply by w_L^{j r}.  Inverse
 // (decimation in time): multiply by conj(w_L^{j r}), then inverse DFT; it
-// undoes the forward pass up to a factor R.  w_L^{j r} = tw[j r n / L],
+// undoes the forward pass up to a factor RD.  w_L^{j r} = tw[j r n / L],
 // an index below n.
-template <int R, bool INV>
-__device__ __forceinline__ void fft_pass(double2* buf, int n, int nb, int L, const double2* __restrict__ tw) {
-  const int lm = ilog2(L / R);
+template <int RD, bool INV, typename C>
+__device__ __forceinline__ void fft_pass(C* buf, int n, int nb, int L, const C* __restrict__ tw) {
+  const int lm = ilog2(L / RD);
   const int m = 1 << lm;
-  const int lpv = ilog2(n / R);
+  const int lpv = ilog2(n / RD);
   const int total = nb << lpv;
   const int tshift = ilog2(n / L);
   for (int b = threadIdx.x; b < total; b += kThreads) {
     const int v = b >> lpv;
-    const int bb = b & ((n / R) - 1);
+    const int bb = b & ((n / RD) - 1);
     const int blk = bb >> lm;
     const int j = bb & (m - 1);
-    double2* p = buf + v * n + blk * L + j;
-    double2 x[R];
+    C* p = buf + v * n + blk * L + j;
+    C x[RD];
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = p[r * m];
+    for (int r = 0; r < RD; ++r) x[r] = p[r * m];
     if (!INV) {
-      dft<R, false>(x);
+      dft<RD, false>(x);
       if (j) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], __ldg(tw + ((j * r) << tshift)));
+        for (int r = 1; r < RD; ++r) x[r] = cmul(x[r], __ldg(tw + ((j * r) << tshift)));
       }
     } else {
       if (j) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) x[r] = cmulc(x[r], __ldg(tw + ((j * r) << tshift)));
+        for (int r = 1; r < RD; ++r) x[r] = cmulc(x[r], __ldg(tw + ((j * r) << tshift)));
       }
-      dft<R, true>(x);
+      dft<RD, true>(x);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) p[r * m] = x[r];
+    for (int r = 0; r < RD; ++r) p[r * m] = x[r];
   }
 }
 
-// Last forward pass (block length R, no twiddles), multiplication by i k / n
+// Last forward pass (block length RD, no twiddles), multiplication by i k / n
 // at the digit-reversed positions, first inverse pass -- all in registers.
-template <int R>
-__device__ __forceinline__ void fft_center(double2* buf, int n, int nb, const double* __restrict__ kd) {
-  const int total = (nb * n) / R;
+template <int RD, typename C, typename R>
+__device__ __forceinline__ void fft_center(C* buf, int n, int nb, const R* __restrict__ kd) {
+  const int total = (nb * n) / RD;
   for (int b = threadIdx.x; b < total; b += kThreads) {
-    double2* p = buf + b * R;
-    const int pos = (b * R) & (n - 1);
-    double2 x[R];
+    C* p = buf + b * RD;
+    const int pos = (b * RD) & (n - 1);
+    C x[RD];
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = p[r];
-    dft<R, false>(x);
+    for (int r = 0; r < RD; ++r) x[r] = p[r];
+    dft<RD, false>(x);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const double k = __ldg(kd + pos + r);
-      x[r] = make_double2(-k * x[r].y, k * x[r].x);
+    for (int r = 0; r < RD; ++r) {
+      const R k = __ldg(kd + pos + r);
+      x[r] = cmk<C>(-k * x[r].y, k * x[r].x);
     }
-    dft<R, true>(x);
+    dft<RD, true>(x);
 #pragma unroll
-    for (int r = 0; r < R; ++r) p[r] = x[r];
+    for (int r = 0; r < RD; ++r) p[r] = x[r];
   }
 }
 
-template <bool INV>
-__device__ __forceinline__ void fft_pass_dispatch(int R, double2* buf, int n, int nb, int L, const double2* tw) {
-  if (R == 8)
+template <bool INV, typename C>
+__device__ __forceinline__ void fft_pass_dispatch(int RD, C* buf, int n, int nb, int L, const C* tw) {
+  if (RD == 8)
     fft_pass<8, INV>(buf, n, nb, L, tw);
-  else if (R == 4)
+  else if (RD == 4)
     fft_pass<4, INV>(buf, n, nb, L, tw);
   else
     fft_pass<2, INV>(buf, n, nb, L, tw);
@@ -218,38 +257,40 @@ __device__ __forceinline__ void fft_pass_dispatch(int R, double2* buf, int n, in
 
 // buf <- D buf for nb vectors (spectral first derivative, Sec. II D):
 // forward FFT, multiply by i k, inverse FFT (1/n folded into kd).
-__device__ __forceinline__ void spectral_derivative(double2* buf, int nb, const InstDesc& I) {
-  const int n = I.n;
+template <typename R>
+__device__ __forceinline__ void spectral_derivative(typename Cx<R>::T* buf, int nb, const HOp<R>& H) {
+  const int n = H.n;
   int L = n;
-  for (int i = 0; i < I.npass - 1; ++i) {
-    fft_pass_dispatch<false>(I.radix[i], buf, n, nb, L, I.tw);
-    L /= I.radix[i];
+  for (int i = 0; i < H.npass - 1; ++i) {
+    fft_pass_dispatch<false>(H.radix[i], buf, n, nb, L, H.tw);
+    L /= H.radix[i];
     __syncthreads();
   }
-  const int Rc = I.radix[I.npass - 1];
+  const int Rc = H.radix[H.npass - 1];
   if (Rc == 8)
-    fft_center<8>(buf, n, nb, I.kd);
+    fft_center<8>(buf, n, nb, H.kd);
   else if (Rc == 4)
-    fft_center<4>(buf, n, nb, I.kd);
+    fft_center<4>(buf, n, nb, H.kd);
   else
-    fft_center<2>(buf, n, nb, I.kd);
+    fft_center<2>(buf, n, nb, H.kd);
   __syncthreads();
-  for (int i = I.npass - 2; i >= 0; --i) {
-    L *= I.radix[i];
-    fft_pass_dispatch<true>(I.radix[i], buf, n, nb, L, I.tw);
+  for (int i = H.npass - 2; i >= 0; --i) {
+    L *= H.radix[i];
+    fft_pass_dispatch<true>(H.radix[i], buf, n, nb, L, H.tw);
     __syncthreads();
   }
 }
 
 // Coupling F_{st}(q_j) from the stored upper triangle.
-__device__ __forceinline__ double coupling(const InstDesc& I, int s, int t, int j) {
-  const int S = I.S;
+template <typename R>
+__device__ __forceinline__ R coupling(const HOp<R>& H, int s, int t, int j) {
+  const int S = H.S;
   if (s < t) {
     const int p = s * S - (s * (s + 1)) / 2 + (t - s - 1);
-    return __ldg(I.F + (size_t)p * I.n + j);
+    return __ldg(H.F + (size_t)p * H.n + j);
   } else {
     const int p = t * S - (t * (t + 1)) / 2 + (s - t - 1);
-    return -__ldg(I.F + (size_t)p * I.n + j);
+    return -__ldg(H.F + (size_t)p * H.n + j);
   }
 }
 
@@ -259,44 +300,47 @@ __device__ __forceinline__ double coupling(const InstDesc& I, int s, int t, int 
 // derivative), so H x is two applications of (D + F): each a forward FFT,
 // a multiplication by i k and an inverse FFT per surface, plus the pointwise
 // coupling -- 4 transforms per surface, as counted in Table I.
-// sbuf holds nb_cap vectors of length n; U = I.work (scratch).  y may alias
-// x or z.  z may be null when e == 0.
-__device__ __forceinline__ void apply_h_axpby(const InstDesc& I, double2* sbuf, int nb_cap, const double2* x,
-                                              double2* y, const double2* z, double e, double a, double2 c) {
-  const int n = I.n, S = I.S;
+// sbuf holds nb_cap vectors of length n; H.U is scratch.  y may alias x or z.
+// z may be null when e == 0.
+template <typename R>
+__device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
+                                              const typename Cx<R>::T* x, typename Cx<R>::T* y,
+                                              const typename Cx<R>::T* z, R e, R a, typename Cx<R>::T c) {
+  using C = typename Cx<R>::T;
+  const int n = H.n, S = H.S;
   const int ln = ilog2(n);
-  double2* U = I.work;
+  C* U = H.U;
   const int nb = (S <= nb_cap) ? S : 1;
   // U = (D + F) x
   for (int s0 = 0; s0 < S; s0 += nb) {
     for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[i] = x[s0 * n + i];
     __syncthreads();
-    spectral_derivative(sbuf, nb, I);
+    spectral_derivative<R>(sbuf, nb, H);
     for (int i = threadIdx.x; i < nb * n; i += kThreads) {
       const int s = s0 + (i >> ln), j = i & (n - 1);
-      double2 acc = sbuf[i];
+      C acc = sbuf[i];
       for (int t = 0; t < S; ++t)
-        if (t != s) acc = caxpy_r(coupling(I, s, t, j), x[t * n + j], acc);
+        if (t != s) acc = caxpy_r(coupling(H, s, t, j), x[t * n + j], acc);
       U[s * n + j] = acc;
     }
     __syncthreads();
   }
   // y = e z + a x + c (-hbar^2/2m (D + F) U + V x)
-  const double mh = -I.h2m;
+  const R mh = -H.h2m;
   for (int s0 = 0; s0 < S; s0 += nb) {
     for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[i] = U[s0 * n + i];
     __syncthreads();
-    spectral_derivative(sbuf, nb, I);
+    spectral_derivative<R>(sbuf, nb, H);
     for (int i = threadIdx.x; i < nb * n; i += kThreads) {
       const int s = s0 + (i >> ln), j = i & (n - 1);
-      double2 acc = sbuf[i];
+      C acc = sbuf[i];
       for (int t = 0; t < S; ++t)
-        if (t != s) acc = caxpy_r(coupling(I, s, t, j), U[t * n + j], acc);
-      const double2 xs = x[s * n + j];
-      const double v = __ldg(I.V + s * n + j);
-      const double2 hx = make_double2(fma(mh, acc.x, v * xs.x), fma(mh, acc.y, v * xs.y));
-      double2 out = caxpy(c, hx, make_double2(a * xs.x, a * xs.y));
-      if (e != 0.0) out = caxpy_r(e, z[s * n + j], out);
+        if (t != s) acc = caxpy_r(coupling(H, s, t, j), U[t * n + j], acc);
+      const C xs = x[s * n + j];
+      const R v = __ldg(H.V + s * n + j);
+      const C hx = cmk<C>(fma(mh, acc.x, v * xs.x), fma(mh, acc.y, v * xs.y));
+      C out = caxpy(c, hx, cmk<C>(a * xs.x, a * xs.y));
+      if (e != (R)0) out = caxpy_r(e, z[s * n + j], out);
       y[s * n + j] = out;
     }
     __syncthreads();

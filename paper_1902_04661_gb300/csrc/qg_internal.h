@@ -36,6 +36,8 @@ struct qg_grid {
   FftPlan plan[2];
   double2* d_tw[2];  // tw[k] = exp(-2 pi i k / n), k = 0..n-1
   double* d_kd[2];   // k of the frequency held at digit-reversed position p, divided by n
+  float2* d_tw32[2];  // the same tables rounded to FP32 (mixed-precision inner solves)
+  float* d_kd32[2];
   int device;
 };
 
@@ -45,6 +47,8 @@ struct qg_model {
   double mass[2];
   double* d_V;  // S * ntot
   double* d_F;  // D * S(S-1)/2 * ntot (upper triangle)
+  float* d_V32;  // FP32 copies for the mixed-precision inner solves
+  float* d_F32;
 };
 
 struct InstDesc;
@@ -55,6 +59,8 @@ struct qg_state {
   int* d_counter;           // work counter of the persistent kernel (device)
   double2* d_psi;    // S * ntot
   double2* d_work;   // (restart_cap + 5) vectors of S * ntot
+  float2* d_work32;  // mixed precision: (restart_cap + 4) FP32 vectors, else null
+  int precision;     // QG_C128 or QG_C64_MIXED
   int restart_cap;
   cudaStream_t stream;
   qg_step_stats* d_stats;   // one record
@@ -77,6 +83,12 @@ struct InstDesc {
   double2* psi;
   double2* work;  // U, B, X, P0, then basis V_0..V_m (each S * n)
   int restart_cap;
+  int precision;  // QG_C128 or QG_C64_MIXED
+  const float2* tw32;
+  const float* kd32;
+  const float* V32;
+  const float* F32;
+  float2* work32;  // mixed: U32, r32, d32, then inner basis (each S * n)
 };
 
 // Parameters of one propagate launch (passed by value).
@@ -91,6 +103,8 @@ struct StepPlan {
   int reorth;
   int mid_epi;
   int true_res;
+  double inner_tol;
+  int max_outer;
   double frac[QG_MAX_FRACTIONS];
 };
 
@@ -118,5 +132,6 @@ cudaError_t qg_launch_gaussian(double2* d_psi, int n, int S, int surface, double
 cudaError_t qg_noalloc_launch(int n, double qmin, double qmax, int S, double mass, const double* V, const double* F,
                               double2* psi, const FftPlan& plan, const StepPlan& P, qg_step_stats* host_stats,
                               cudaStream_t st);
+cudaError_t qg_launch_to_f32(const double* d_in, float* d_out, size_t n, cudaStream_t st);
 cudaError_t qg_launch_fields2(const double* d_W, const double* d_dW, int n, double* d_V, double* d_F,
                               cudaStream_t st);

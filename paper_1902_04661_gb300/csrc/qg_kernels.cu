@@ -1,5 +1,6 @@
 // Kernels of libqgeom: the persistent propagator (composed trapezoidal /
-// implicit-midpoint steps with GMRES implicit solves), the Hamiltonian action,
+// implicit-midpoint steps with GMRES implicit solves, in FP64 or with
+// complex64 inner solves refined in FP64), the Hamiltonian action,
 // observables, the Gaussian initial state and the two-state diabatic ->
 // adiabatic field builder.
 #include <cuda_runtime.h>
@@ -8,106 +9,171 @@
 
 namespace qg {
 
-// Shared-memory layout of one CTA (dynamic part).
-struct Smem {
-  double2* fft;    // nb_cap * max_n
-  double2* hess;   // (m + 1) * m, column j at hess + j * (m + 1)
-  double2* g;      // m + 1
-  double2* gs;     // m   Givens s
-  double* gc;      // m   Givens c
-  double2* y;      // m
-  int nb_cap;
+__device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Small GMRES arrays of one precision in shared memory.
+template <typename R>
+struct GSmem {
+  using C = typename Cx<R>::T;
+  C* hess;   // (m + 1) * m, column j at hess + j * (m + 1)
+  C* g;      // m + 1
+  C* gs;     // m   Givens s
+  R* gc;     // m   Givens c
+  C* y;      // m
 };
 
-__device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+// Dynamic shared memory: the FFT buffer (nb_cap vectors of max_n complex
+// doubles, also used by the FP32 passes), then the GMRES arrays sized for
+// doubles (the FP32 arrays fit in the same space).
+struct Smem {
+  unsigned char* fft;
+  unsigned char* gm;
+  int nb_cap;
+  int m;
+};
 
 __device__ Smem carve_smem(void* base, int max_n, int nb_cap, int m) {
   Smem s;
-  char* p = reinterpret_cast<char*>(base);
-  s.fft = reinterpret_cast<double2*>(p);
-  p += align16(sizeof(double2) * (size_t)nb_cap * max_n);
-  s.hess = reinterpret_cast<double2*>(p);
-  p += align16(sizeof(double2) * (size_t)(m + 1) * m);
-  s.g = reinterpret_cast<double2*>(p);
-  p += align16(sizeof(double2) * (size_t)(m + 1));
-  s.gs = reinterpret_cast<double2*>(p);
-  p += align16(sizeof(double2) * (size_t)m);
-  s.y = reinterpret_cast<double2*>(p);
-  p += align16(sizeof(double2) * (size_t)m);
-  s.gc = reinterpret_cast<double*>(p);
+  unsigned char* p = reinterpret_cast<unsigned char*>(base);
+  s.fft = p;
+  s.gm = p + align16(sizeof(double2) * (size_t)nb_cap * max_n);
   s.nb_cap = nb_cap;
+  s.m = m;
   return s;
+}
+
+template <typename R>
+__device__ GSmem<R> gsmem(const Smem& s) {
+  using C = typename Cx<R>::T;
+  GSmem<R> g;
+  const int m = s.m;
+  unsigned char* p = s.gm;
+  g.hess = reinterpret_cast<C*>(p);
+  p += align16(sizeof(double2) * (size_t)(m + 1) * m);
+  g.g = reinterpret_cast<C*>(p);
+  p += align16(sizeof(double2) * (size_t)(m + 1));
+  g.gs = reinterpret_cast<C*>(p);
+  p += align16(sizeof(double2) * (size_t)m);
+  g.y = reinterpret_cast<C*>(p);
+  p += align16(sizeof(double2) * (size_t)m);
+  g.gc = reinterpret_cast<R*>(p);
+  return g;
 }
 
 struct Counters {
   long long hpsi;
+  long long hpsi32;
   long long krylov;
   long long ortho;
   long long update;
   long long restart;
+  long long outer;
   int max_krylov;
   double max_res;
 };
 
+// H psi operands of an instance in one precision; scratch vector U given.
+__device__ __forceinline__ HOp<double> hop64(const InstDesc& I, double2* U) {
+  HOp<double> H;
+  H.n = I.n;
+  H.S = I.S;
+  H.npass = I.npass;
+  for (int i = 0; i < QG_MAX_PASSES; ++i) H.radix[i] = I.radix[i];
+  H.h2m = I.h2m;
+  H.tw = I.tw;
+  H.kd = I.kd;
+  H.V = I.V;
+  H.F = I.F;
+  H.U = U;
+  return H;
+}
+
+__device__ __forceinline__ HOp<float> hop32(const InstDesc& I, float2* U) {
+  HOp<float> H;
+  H.n = I.n;
+  H.S = I.S;
+  H.npass = I.npass;
+  for (int i = 0; i < QG_MAX_PASSES; ++i) H.radix[i] = I.radix[i];
+  H.h2m = (float)I.h2m;
+  H.tw = I.tw32;
+  H.kd = I.kd32;
+  H.V = I.V32;
+  H.F = I.F32;
+  H.U = U;
+  return H;
+}
+
+struct SolveParams {
+  double tol;
+  int m;
+  int max_iters;
+  int reorth;
+  int true_res;
+};
+
 // Solve (1 + i tau H) x = b by restarted GMRES (Sec. II B) in the grid inner
-// product.  X holds the initial guess on entry and the solution on exit.
-// Returns true on convergence (estimated relative residual <= tol).
-__device__ bool gmres_solve(const InstDesc& I, const Smem& sm, const StepPlan& P, double tau, const double2* b,
-                            double2* X, Counters& cnt, double* red, double* sc) {
-  const int len = I.S * I.n;
-  const double dv = I.dq;
-  const int m = P.restart;
-  double2* basis = I.work + (size_t)4 * len;
-  const double2 ic = make_double2(0.0, tau);     // A = 1 + i tau H
-  const double2 mic = make_double2(0.0, -tau);
-  const double bn = sqrt(dv * cta_norm2(b, len, red, sc));
-  const double target = P.tol * bn;
+// product, in precision R.  X holds the initial guess on entry and the
+// solution on exit; basis holds m + 1 vectors.  Returns true on convergence
+// (estimated relative residual <= tol).  *res_out receives the final
+// relative residual estimate.
+template <typename R>
+__device__ bool gmres_solve(const HOp<R>& H, const Smem& smem, const SolveParams& P, R dv, R tau,
+                            const typename Cx<R>::T* b, typename Cx<R>::T* X, typename Cx<R>::T* basis,
+                            Counters& cnt, R* red, R* sc, double* res_out) {
+  using C = typename Cx<R>::T;
+  const GSmem<R> sm = gsmem<R>(smem);
+  C* fbuf = reinterpret_cast<C*>(smem.fft);
+  const int nbc = sizeof(R) == 8 ? smem.nb_cap : 2 * smem.nb_cap;
+  const int len = H.S * H.n;
+  const int m = P.m;
+  const C ic = cmk<C>((R)0, tau);     // A = 1 + i tau H
+  const C mic = cmk<C>((R)0, -tau);
+  const R bn = sqrt(dv * cta_norm2(b, len, red, sc));
+  const R target = (R)P.tol * bn;
   int total = 0;
-  int this_solve = 0;
   // r0 = b - A X
-  apply_h_axpby(I, sm.fft, sm.nb_cap, X, basis, b, 1.0, -1.0, mic);
-  cnt.hpsi++;
+  apply_h_axpby<R>(H, fbuf, nbc, X, basis, b, (R)1, (R)-1, mic);
+  if (sizeof(R) == 8) cnt.hpsi++; else cnt.hpsi32++;
   for (int guard = 0; guard < P.max_iters + 2; ++guard) {
-    double2* V0 = basis;
-    const double beta = sqrt(dv * cta_norm2(V0, len, red, sc));
-    if (beta <= target || bn == 0.0) {
-      double r = (bn > 0.0) ? beta / bn : 0.0;
-      if (r > cnt.max_res) cnt.max_res = r;
-      if (this_solve > cnt.max_krylov) cnt.max_krylov = this_solve;
+    C* V0 = basis;
+    const R beta = sqrt(dv * cta_norm2(V0, len, red, sc));
+    if (beta <= target || bn == (R)0) {
+      *res_out = (bn > (R)0) ? (double)(beta / bn) : 0.0;
+      if (total > cnt.max_krylov) cnt.max_krylov = total;
       return true;
     }
     if (total >= P.max_iters) break;
-    const double ib = 1.0 / beta;
+    const R ib = (R)1 / beta;
     for (int i = threadIdx.x; i < len; i += kThreads) V0[i] = cscale(ib, V0[i]);
     if (threadIdx.x == 0) {
-      sm.g[0] = make_double2(beta, 0.0);
-      for (int i = 1; i <= m; ++i) sm.g[i] = make_double2(0.0, 0.0);
+      sm.g[0] = cmk<C>(beta, (R)0);
+      for (int i = 1; i <= m; ++i) sm.g[i] = cmk<C>((R)0, (R)0);
     }
     __syncthreads();
     int ncol = 0;
     bool conv = false;
-    double res_est = beta;
+    R res_est = beta;
     for (int j = 0; j < m; ++j) {
-      double2* Vj = basis + (size_t)j * len;
-      double2* W = basis + (size_t)(j + 1) * len;
-      apply_h_axpby(I, sm.fft, sm.nb_cap, Vj, W, nullptr, 0.0, 1.0, ic);
-      cnt.hpsi++;
-      double2* hcol = sm.hess + (size_t)j * (m + 1);
-      if (threadIdx.x <= j + 1) hcol[threadIdx.x] = make_double2(0.0, 0.0);
+      C* Vj = basis + (size_t)j * len;
+      C* W = basis + (size_t)(j + 1) * len;
+      apply_h_axpby<R>(H, fbuf, nbc, Vj, W, nullptr, (R)0, (R)1, ic);
+      if (sizeof(R) == 8) cnt.hpsi++; else cnt.hpsi32++;
+      C* hcol = sm.hess + (size_t)j * (m + 1);
+      if (threadIdx.x <= j + 1) hcol[threadIdx.x] = cmk<C>((R)0, (R)0);
       __syncthreads();
       // Classical Gram-Schmidt, optionally repeated once (CGS2).
       for (int pass = 0; pass < (P.reorth ? 2 : 1); ++pass) {
         for (int c0 = 0; c0 <= j; c0 += 8) {
           const int nc = min(8, j + 1 - c0);
-          double v[16];
+          R v[16];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) v[k] = 0.0;
+          for (int k = 0; k < 16; ++k) v[k] = (R)0;
           for (int i = threadIdx.x; i < len; i += kThreads) {
-            const double2 w = W[i];
+            const C w = W[i];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
               if (k < nc) {
-                const double2 q = basis[(size_t)(c0 + k) * len + i];
+                const C q = basis[(size_t)(c0 + k) * len + i];
                 v[2 * k] = fma(q.x, w.x, fma(q.y, w.y, v[2 * k]));
                 v[2 * k + 1] = fma(q.x, w.y, fma(-q.y, w.x, v[2 * k + 1]));
               }
@@ -115,18 +181,19 @@ __device__ bool gmres_solve(const InstDesc& I, const Smem& sm, const StepPlan& P
           }
           cta_sum<16>(v, red, sc);
           if (threadIdx.x < nc) {
-            const double2 h = make_double2(dv * sc[2 * threadIdx.x], dv * sc[2 * threadIdx.x + 1]);
+            const C h = cmk<C>(dv * sc[2 * threadIdx.x], dv * sc[2 * threadIdx.x + 1]);
             hcol[c0 + threadIdx.x] = cadd(hcol[c0 + threadIdx.x], h);
             sc[32 + 2 * threadIdx.x] = h.x;
             sc[33 + 2 * threadIdx.x] = h.y;
           }
           __syncthreads();
-          double2 hk[8];
+          C hk[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) hk[k] = (k < nc) ? make_double2(sc[32 + 2 * k], sc[33 + 2 * k]) : make_double2(0, 0);
+          for (int k = 0; k < 8; ++k)
+            hk[k] = (k < nc) ? cmk<C>(sc[32 + 2 * k], sc[33 + 2 * k]) : cmk<C>((R)0, (R)0);
           __syncthreads();
           for (int i = threadIdx.x; i < len; i += kThreads) {
-            double2 w = W[i];
+            C w = W[i];
 #pragma unroll
             for (int k = 0; k < 8; ++k)
               if (k < nc) w = cnaxpy(hk[k], basis[(size_t)(c0 + k) * len + i], w);
@@ -135,50 +202,51 @@ __device__ bool gmres_solve(const InstDesc& I, const Smem& sm, const StepPlan& P
           __syncthreads();
         }
       }
-      const double hn = sqrt(dv * cta_norm2(W, len, red, sc));
-      if (hn > 1e-300) {
-        const double ih = 1.0 / hn;
+      const R hn = sqrt(dv * cta_norm2(W, len, red, sc));
+      const R tiny = sizeof(R) == 8 ? (R)1e-300 : (R)1e-35;
+      if (hn > tiny) {
+        const R ih = (R)1 / hn;
         for (int i = threadIdx.x; i < len; i += kThreads) W[i] = cscale(ih, W[i]);
       }
       if (threadIdx.x == 0) {
-        hcol[j + 1] = make_double2(hn, 0.0);
+        hcol[j + 1] = cmk<C>(hn, (R)0);
         // previous rotations
         for (int i = 0; i < j; ++i) {
-          const double c = sm.gc[i];
-          const double2 s = sm.gs[i];
-          const double2 h0 = hcol[i], h1 = hcol[i + 1];
-          const double2 t = caxpy(s, h1, cscale(c, h0));                       // c h0 + s h1
-          const double2 u = cnaxpy(make_double2(s.x, -s.y), h0, cscale(c, h1));  // -conj(s) h0 + c h1
+          const R c = sm.gc[i];
+          const C s = sm.gs[i];
+          const C h0 = hcol[i], h1 = hcol[i + 1];
+          const C t = caxpy(s, h1, cscale(c, h0));                    // c h0 + s h1
+          const C u = cnaxpy(cmk<C>(s.x, -s.y), h0, cscale(c, h1));   // -conj(s) h0 + c h1
           hcol[i] = t;
           hcol[i + 1] = u;
         }
         // new rotation zeroing hcol[j+1]
-        const double2 a = hcol[j];
-        const double bb = hcol[j + 1].x;
-        const double aa = hypot(a.x, a.y);
-        double c;
-        double2 s, r;
-        if (bb == 0.0) {
-          c = 1.0;
-          s = make_double2(0.0, 0.0);
+        const C a = hcol[j];
+        const R bb = hcol[j + 1].x;
+        const R aa = hypot(a.x, a.y);
+        R c;
+        C s, r;
+        if (bb == (R)0) {
+          c = (R)1;
+          s = cmk<C>((R)0, (R)0);
           r = a;
-        } else if (aa == 0.0) {
-          c = 0.0;
-          s = make_double2(1.0, 0.0);
-          r = make_double2(bb, 0.0);
+        } else if (aa == (R)0) {
+          c = (R)0;
+          s = cmk<C>((R)1, (R)0);
+          r = cmk<C>(bb, (R)0);
         } else {
-          const double rho = hypot(aa, bb);
-          const double2 ph = make_double2(a.x / aa, a.y / aa);
+          const R rho = hypot(aa, bb);
+          const C ph = cmk<C>(a.x / aa, a.y / aa);
           c = aa / rho;
-          s = make_double2(ph.x * bb / rho, ph.y * bb / rho);
-          r = make_double2(ph.x * rho, ph.y * rho);
+          s = cmk<C>(ph.x * bb / rho, ph.y * bb / rho);
+          r = cmk<C>(ph.x * rho, ph.y * rho);
         }
         sm.gc[j] = c;
         sm.gs[j] = s;
         hcol[j] = r;
-        hcol[j + 1] = make_double2(0.0, 0.0);
-        const double2 gj = sm.g[j];
-        sm.g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
+        hcol[j + 1] = cmk<C>((R)0, (R)0);
+        const C gj = sm.g[j];
+        sm.g[j + 1] = cmk<C>(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
         sm.g[j] = cscale(c, gj);
         sc[0] = hypot(sm.g[j + 1].x, sm.g[j + 1].y);
       }
@@ -188,51 +256,136 @@ __device__ bool gmres_solve(const InstDesc& I, const Smem& sm, const StepPlan& P
       ncol = j + 1;
       cnt.ortho += j + 1;
       total++;
-      this_solve++;
       cnt.krylov++;
       if (res_est <= target) {
         conv = true;
         break;
       }
-      if (total >= P.max_iters || hn <= 1e-300) break;
+      if (total >= P.max_iters || hn <= tiny) break;
     }
     // y = R^{-1} g (upper triangular ncol x ncol)
     if (threadIdx.x == 0) {
       for (int i = ncol - 1; i >= 0; --i) {
-        double2 acc = sm.g[i];
+        C acc = sm.g[i];
         for (int k = i + 1; k < ncol; ++k) acc = cnaxpy(sm.hess[(size_t)k * (m + 1) + i], sm.y[k], acc);
-        const double2 d = sm.hess[(size_t)i * (m + 1) + i];
-        const double dd = 1.0 / fma(d.x, d.x, d.y * d.y);
-        sm.y[i] = make_double2((acc.x * d.x + acc.y * d.y) * dd, (acc.y * d.x - acc.x * d.y) * dd);
+        const C d = sm.hess[(size_t)i * (m + 1) + i];
+        const R dd = (R)1 / fma(d.x, d.x, d.y * d.y);
+        sm.y[i] = cmk<C>((acc.x * d.x + acc.y * d.y) * dd, (acc.y * d.x - acc.x * d.y) * dd);
       }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < len; i += kThreads) {
-      double2 x = X[i];
+      C x = X[i];
       for (int k = 0; k < ncol; ++k) x = caxpy(sm.y[k], basis[(size_t)k * len + i], x);
       X[i] = x;
     }
     cnt.update += ncol;
     __syncthreads();
     if (conv && !P.true_res) {
-      const double r = (bn > 0.0) ? res_est / bn : 0.0;
-      if (r > cnt.max_res) cnt.max_res = r;
-      if (this_solve > cnt.max_krylov) cnt.max_krylov = this_solve;
+      *res_out = (bn > (R)0) ? (double)(res_est / bn) : 0.0;
+      if (total > cnt.max_krylov) cnt.max_krylov = total;
       return true;
     }
     if (total >= P.max_iters && !conv) break;
     // restart (or true-residual check): V0 = b - A X
-    apply_h_axpby(I, sm.fft, sm.nb_cap, X, basis, b, 1.0, -1.0, mic);
-    cnt.hpsi++;
+    apply_h_axpby<R>(H, fbuf, nbc, X, basis, b, (R)1, (R)-1, mic);
+    if (sizeof(R) == 8) cnt.hpsi++; else cnt.hpsi32++;
     cnt.restart++;
   }
-  if (this_solve > cnt.max_krylov) cnt.max_krylov = this_solve;
+  if (total > cnt.max_krylov) cnt.max_krylov = total;
+  *res_out = 1e300;
+  return false;
+}
+
+template <typename C>
+__device__ __forceinline__ void vcopy(C* dst, const C* src, int len) {
+  for (int i = threadIdx.x; i < len; i += kThreads) dst[i] = src[i];
+  __syncthreads();
+}
+
+// FP64 implicit solve (1 + i tau H) X = b with GMRES in FP64.
+__device__ bool solve_fp64(const InstDesc& I, const Smem& sm, const StepPlan& P, double tau, const double2* b,
+                           double2* X, Counters& cnt, double* red, double* sc) {
+  const int len = I.S * I.n;
+  const HOp<double> H = hop64(I, I.work);
+  SolveParams sp{P.tol, P.restart, P.max_iters, P.reorth, P.true_res};
+  double res = 0.0;
+  const bool ok = gmres_solve<double>(H, sm, sp, I.dq, tau, b, X, I.work + (size_t)4 * len, cnt, red, sc, &res);
+  if (ok && res > cnt.max_res) cnt.max_res = res;
+  if (!ok) cnt.max_res = 1e300;
+  return ok;
+}
+
+// Mixed-precision implicit solve: FP64 residual r = b - (1 + i tau H) X,
+// complex64 GMRES for (1 + i tau H) d = r / ||r|| to inner_tol, X += ||r|| d,
+// until ||r|| <= tol ||b||.
+__device__ bool solve_mixed(const InstDesc& I, const Smem& sm, const StepPlan& P, double tau, const double2* b,
+                            double2* X, Counters& cnt, double* red, double* sc) {
+  const int len = I.S * I.n;
+  const HOp<double> H64 = hop64(I, I.work);
+  double2* Rv = I.work + (size_t)4 * len;          // FP64 residual
+  const HOp<float> H32 = hop32(I, I.work32);
+  float2* r32 = I.work32 + (size_t)1 * len;
+  float2* d32 = I.work32 + (size_t)2 * len;
+  float2* basis32 = I.work32 + (size_t)3 * len;
+  float* redf = reinterpret_cast<float*>(red);
+  float* scf = reinterpret_cast<float*>(sc);
+  const double2 mic = make_double2(0.0, -tau);
+  const double dv = I.dq;
+  const double bn = sqrt(dv * cta_norm2(b, len, red, sc));
+  const double target = P.tol * bn;
+  SolveParams sp{P.inner_tol, P.restart, P.max_iters, P.reorth, 0};
+  for (int outer = 0; outer <= P.max_outer; ++outer) {
+    apply_h_axpby<double>(H64, reinterpret_cast<double2*>(sm.fft), sm.nb_cap, X, Rv, b, 1.0, -1.0, mic);
+    cnt.hpsi++;
+    const double rho = sqrt(dv * cta_norm2(Rv, len, red, sc));
+    if (rho <= target || bn == 0.0) {
+      const double r = bn > 0.0 ? rho / bn : 0.0;
+      if (r > cnt.max_res) cnt.max_res = r;
+      return true;
+    }
+    if (outer == P.max_outer) break;
+    cnt.outer++;
+    const double ir = 1.0 / rho;
+    for (int i = threadIdx.x; i < len; i += kThreads) {
+      const double2 v = Rv[i];
+      r32[i] = make_float2((float)(v.x * ir), (float)(v.y * ir));
+      d32[i] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    double res = 0.0;
+    gmres_solve<float>(H32, sm, sp, (float)dv, (float)tau, r32, d32, basis32, cnt, redf, scf, &res);
+    for (int i = threadIdx.x; i < len; i += kThreads) {
+      const float2 d = d32[i];
+      const double2 x = X[i];
+      X[i] = make_double2(fma(rho, (double)d.x, x.x), fma(rho, (double)d.y, x.y));
+    }
+    __syncthreads();
+  }
   cnt.max_res = 1e300;
   return false;
 }
 
-__device__ __forceinline__ void vcopy(double2* dst, const double2* src, int len) {
-  for (int i = threadIdx.x; i < len; i += kThreads) dst[i] = src[i];
+// Explicit-Euler initial guess X = (1 - i tau H) src, in complex64 for the
+// mixed-precision form (only the starting point of the refinement).
+__device__ void guess_mixed(const InstDesc& I, const Smem& sm, double tau, const double2* src, double2* X,
+                            Counters& cnt) {
+  const int len = I.S * I.n;
+  const HOp<float> H32 = hop32(I, I.work32);
+  float2* s32 = I.work32 + (size_t)1 * len;
+  float2* y32 = I.work32 + (size_t)2 * len;
+  for (int i = threadIdx.x; i < len; i += kThreads) {
+    const double2 v = src[i];
+    s32[i] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  apply_h_axpby<float>(H32, reinterpret_cast<float2*>(sm.fft), 2 * sm.nb_cap, s32, y32, nullptr, 0.f, 1.f,
+                       make_float2(0.f, (float)-tau));
+  cnt.hpsi32++;
+  for (int i = threadIdx.x; i < len; i += kThreads) {
+    const float2 y = y32[i];
+    X[i] = make_double2((double)y.x, (double)y.y);
+  }
   __syncthreads();
 }
 
@@ -240,11 +393,14 @@ __device__ __forceinline__ void vcopy(double2* dst, const double2* src, int len)
 __device__ void run_instance(const InstDesc& I, const StepPlan& P, const Smem& sm, qg_step_stats* st, double* red,
                              double* sc) {
   const int len = I.S * I.n;
+  const bool mixed = I.precision == QG_C64_MIXED;
   double2* psi = I.psi;
   double2* B = I.work + (size_t)1 * len;
   double2* X = I.work + (size_t)2 * len;
   double2* P0 = I.work + (size_t)3 * len;
-  Counters cnt{0, 0, 0, 0, 0, 0, 0.0};
+  const HOp<double> H64 = hop64(I, I.work);
+  double2* fb = reinterpret_cast<double2*>(sm.fft);
+  Counters cnt{0, 0, 0, 0, 0, 0, 0, 0, 0.0};
   long long nsub = 0;
   long long failed = -1;
   vcopy(P0, psi, len);
@@ -255,20 +411,31 @@ __device__ void run_instance(const InstDesc& I, const StepPlan& P, const Smem& s
       bool ok;
       if (P.method == QG_TRAPEZOIDAL) {
         // b = (1 - i tau H) psi ; guess x0 = (1 - i tau H) b ; solve (1 + i tau H) x = b
-        apply_h_axpby(I, sm.fft, sm.nb_cap, psi, B, nullptr, 0.0, 1.0, mic);
-        apply_h_axpby(I, sm.fft, sm.nb_cap, B, X, nullptr, 0.0, 1.0, mic);
-        cnt.hpsi += 2;
-        ok = gmres_solve(I, sm, P, tau, B, X, cnt, red, sc);
+        apply_h_axpby<double>(H64, fb, sm.nb_cap, psi, B, nullptr, 0.0, 1.0, mic);
+        cnt.hpsi += 1;
+        if (mixed) {
+          guess_mixed(I, sm, tau, B, X, cnt);
+          ok = solve_mixed(I, sm, P, tau, B, X, cnt, red, sc);
+        } else {
+          apply_h_axpby<double>(H64, fb, sm.nb_cap, B, X, nullptr, 0.0, 1.0, mic);
+          cnt.hpsi += 1;
+          ok = solve_fp64(I, sm, P, tau, B, X, cnt, red, sc);
+        }
         if (ok) vcopy(psi, X, len);
       } else {
         // guess chi0 = (1 - i tau H) psi ; solve (1 + i tau H) chi = psi ;
         // psi' = (1 - i tau H) chi  (or 2 chi - psi)
-        apply_h_axpby(I, sm.fft, sm.nb_cap, psi, X, nullptr, 0.0, 1.0, mic);
-        cnt.hpsi += 1;
-        ok = gmres_solve(I, sm, P, tau, psi, X, cnt, red, sc);
+        if (mixed) {
+          guess_mixed(I, sm, tau, psi, X, cnt);
+          ok = solve_mixed(I, sm, P, tau, psi, X, cnt, red, sc);
+        } else {
+          apply_h_axpby<double>(H64, fb, sm.nb_cap, psi, X, nullptr, 0.0, 1.0, mic);
+          cnt.hpsi += 1;
+          ok = solve_fp64(I, sm, P, tau, psi, X, cnt, red, sc);
+        }
         if (ok) {
           if (P.mid_epi) {
-            apply_h_axpby(I, sm.fft, sm.nb_cap, X, psi, nullptr, 0.0, 1.0, mic);
+            apply_h_axpby<double>(H64, fb, sm.nb_cap, X, psi, nullptr, 0.0, 1.0, mic);
             cnt.hpsi += 1;
           } else {
             for (int i = threadIdx.x; i < len; i += kThreads) {
@@ -298,6 +465,8 @@ __device__ void run_instance(const InstDesc& I, const StepPlan& P, const Smem& s
     st->n_ortho = cnt.ortho;
     st->n_update = cnt.update;
     st->n_restart = cnt.restart;
+    st->n_hpsi32 = cnt.hpsi32;
+    st->n_outer = cnt.outer;
   }
 }
 
@@ -324,8 +493,9 @@ __global__ void __launch_bounds__(QG_THREADS, 1)
     apply_h_kernel(const InstDesc* __restrict__ inst, double2* out, int nb_cap) {
   extern __shared__ __align__(16) unsigned char dyn[];
   const InstDesc I = *inst;
-  apply_h_axpby(I, reinterpret_cast<double2*>(dyn), nb_cap, I.psi, out, nullptr, 0.0, 0.0,
-                make_double2(1.0, 0.0));
+  const HOp<double> H = hop64(I, I.work);
+  apply_h_axpby<double>(H, reinterpret_cast<double2*>(dyn), nb_cap, I.psi, out, nullptr, 0.0, 0.0,
+                        make_double2(1.0, 0.0));
 }
 
 // <psi|H|psi> with H psi written to the scratch vector B of the workspace.
@@ -337,7 +507,9 @@ __global__ void __launch_bounds__(QG_THREADS, 1)
   const InstDesc I = *inst;
   const int len = I.S * I.n;
   double2* Hx = I.work + (size_t)1 * len;
-  apply_h_axpby(I, reinterpret_cast<double2*>(dyn), nb_cap, I.psi, Hx, nullptr, 0.0, 0.0, make_double2(1.0, 0.0));
+  const HOp<double> H = hop64(I, I.work);
+  apply_h_axpby<double>(H, reinterpret_cast<double2*>(dyn), nb_cap, I.psi, Hx, nullptr, 0.0, 0.0,
+                        make_double2(1.0, 0.0));
   double v[2] = {0.0, 0.0};
   for (int i = threadIdx.x; i < len; i += kThreads) {
     const double2 p = I.psi[i], h = Hx[i];
@@ -427,6 +599,11 @@ __global__ void fields2_kernel(const double* __restrict__ W, const double* __res
   F[j] = -f12;
 }
 
+__global__ void to_f32_kernel(const double* __restrict__ in, float* out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
 }  // namespace qg
 
 // ---------------------------------------------------------------------------
@@ -496,6 +673,12 @@ cudaError_t qg_launch_overlap(const double2* d_a, const double2* d_b, int len, d
 cudaError_t qg_launch_gaussian(double2* d_psi, int n, int S, int surface, double qmin, double dq, double q0,
                                double p0, double sigma0, cudaStream_t st) {
   qg::gaussian_kernel<<<1, QG_THREADS, 0, st>>>(d_psi, n, S, surface, qmin, dq, q0, p0, sigma0);
+  return cudaGetLastError();
+}
+
+cudaError_t qg_launch_to_f32(const double* d_in, float* d_out, size_t n, cudaStream_t st) {
+  const int blocks = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  qg::to_f32_kernel<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(d_in, d_out, n);
   return cudaGetLastError();
 }
 
@@ -584,6 +767,12 @@ __global__ void __launch_bounds__(QG_THREADS, 1)
   I.psi = in.psi;
   I.work = reinterpret_cast<double2*>(base);
   I.restart_cap = QG_NA_MAX_RESTART;
+  I.precision = QG_C128;
+  I.tw32 = nullptr;
+  I.kd32 = nullptr;
+  I.V32 = nullptr;
+  I.F32 = nullptr;
+  I.work32 = nullptr;
   qg_step_stats* st = reinterpret_cast<qg_step_stats*>(base + kNaWorkBytes + kNaTwBytes + kNaKdBytes);
   const Smem sm = carve_smem(dyn, in.n, nb_cap, P.restart);
   run_instance(I, P, sm, st, red, sc);
