@@ -70,3 +70,51 @@ def test_nai_like_recipe_reproduces_printed_gaussian():
     omega = np.sqrt(k / wl.NAI_REDUCED_MASS)
     sigma = np.sqrt(1.0 / (2 * wl.NAI_REDUCED_MASS * omega))
     assert abs(sigma - wl.NAI_SIGMA0) < 1e-6
+
+
+def _three_state(q):
+    # three displaced harmonic diabats with smooth positive couplings
+    kf = 0.05
+    w = [0.5 * kf * (q - 0.8) ** 2, 0.5 * kf * (q + 0.6) ** 2 + 0.01, 0.5 * kf * q ** 2 + 0.03]
+    dw = [kf * (q - 0.8), kf * (q + 0.6), kf * q]
+    cpl, dcpl = {}, {}
+    for (a, b), (c, x0) in {(0, 1): (0.004, 0.1), (0, 2): (0.003, 1.0), (1, 2): (0.005, -0.8)}.items():
+        g = c * np.exp(-(q - x0) ** 2 / 2.0) + 0.001
+        cpl[(a, b)] = g
+        dcpl[(a, b)] = -(q - x0) * (g - 0.001)
+    W = np.stack([w[0], cpl[(0, 1)], cpl[(0, 2)], w[1], cpl[(1, 2)], w[2]])
+    dW = np.stack([dw[0], dcpl[(0, 1)], dcpl[(0, 2)], dw[1], dcpl[(1, 2)], dw[2]])[None]
+    return W, dW
+
+
+def test_three_state_adiabatic_hamiltonian_has_the_diabatic_spectrum():
+    from oracle import hamiltonian as ham
+    qmin, qmax, n, m = -9.0, 9.0, 480, 400.0
+    q, dq = grid.points(qmin, qmax, n)
+    W, dW = _three_state(q)
+    V, F, _ = fields.general_adiabatic(W, dW, 3)
+    Ha = ham.dense_h([qmin], [qmax], [n], [m], V, F)
+    D = grid.derivative_matrix(qmin, qmax, n)
+    T = -(D @ D) / (2 * m)
+    M = fields.unpack_symmetric(W, 3)
+    Hd = np.kron(np.eye(3), T).astype(complex)
+    for a in range(3):
+        for b in range(3):
+            Hd[a * n:(a + 1) * n, b * n:(b + 1) * n] += np.diag(M[:, a, b])
+    ea = np.linalg.eigvalsh(Ha)[:20]
+    ed = np.linalg.eigvalsh(Hd)[:20]
+    np.testing.assert_allclose(ea, ed, rtol=0, atol=1e-9)
+
+
+def test_three_state_coupling_is_the_derivative_of_the_eigenvectors():
+    q = np.linspace(-3.0, 3.0, 30001)
+    W, dW = _three_state(q)
+    V, F, vecs = fields.general_adiabatic(W, dW, 3)
+    h = q[1] - q[0]
+    dvec = (vecs[2:] - vecs[:-2]) / (2 * h)
+    t = 0
+    for i in range(3):
+        for k in range(i + 1, 3):
+            fd = np.einsum("ja,ja->j", vecs[1:-1, :, i], dvec[:, :, k])
+            assert np.abs(fd - F[0, t, 1:-1]).max() < 1e-4 * max(1.0, np.abs(F[0, t]).max())
+            t += 1

@@ -79,3 +79,26 @@ def test_matrix_free_action_equals_dense_matrix():
     a = ham.apply_h(H, psi)
     b = ham.apply_h_matrix_free(1.0, 9.0, n, 5.0, V, F, psi)
     assert np.linalg.norm(a - b) < 1e-12 * np.linalg.norm(a)
+
+
+def test_two_dimensional_adiabatic_hamiltonian_has_the_diabatic_spectrum():
+    # D = 2 (Eq. adiab_mol_ham with a 2-vector of couplings): the adiabatic H
+    # built from the two-state fields has the spectrum of p.m^-1.p/2 + W(q)
+    p = dict(wl.MODEL2D_PARAMS, qmin=(-3.5, -3.0), qmax=(3.5, 3.0), mass=(400.0, 400.0), c=0.01)
+    ns = (32, 32)
+    q1 = grid.points(p["qmin"][0], p["qmax"][0], ns[0])[0]
+    q2 = grid.points(p["qmin"][1], p["qmax"][1], ns[1])[0]
+    W, dW = wl.model2d_diabatic(q1, q2, p)
+    V, F = fields.two_state(W, dW)
+    Ha = ham.dense_h(list(p["qmin"]), list(p["qmax"]), list(ns), list(p["mass"]), V, F)
+    N = ns[0] * ns[1]
+    T = np.zeros((N, N), dtype=complex)
+    for d in range(2):
+        Dd = grid.derivative_along(d, list(p["qmin"]), list(p["qmax"]), list(ns))
+        T += -(Dd @ Dd) / (2 * p["mass"][d])
+    Hd = np.kron(np.eye(2), T)
+    Hd[:N, :N] += np.diag(W[0].reshape(-1))
+    Hd[N:, N:] += np.diag(W[2].reshape(-1))
+    Hd[:N, N:] += np.diag(W[1].reshape(-1))
+    Hd[N:, :N] += np.diag(W[1].reshape(-1))
+    np.testing.assert_allclose(np.linalg.eigvalsh(Ha)[:10], np.linalg.eigvalsh(Hd)[:10], rtol=0, atol=5e-8)
