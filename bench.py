@@ -27,13 +27,14 @@ import numpy as np  # noqa: E402
 
 METRIC = "Hψ grid-point-applications/s and propagated steps/s at error 1e-10; % HBM peak"
 
-# Operating point: NaI-like model on the paper's grid, implicit midpoint
-# composed by Suzuki's fractal.  (order, dt) is the cheapest measured point
-# whose convergence error ||psi_dt(t_f) - psi_dt/2(t_f)|| at t_f = 10500 a.u.
-# is below 1e-10 (operating point).
-WORKLOAD = dict(name="nai_like_n2048_s2_midpoint_suzuki", N=2048, S=2, method=1, order=6, scheme=1,
-                dt_fs=0.5, tol=1e-12, restart=30)
 FS = 41.341373335182
+# Operating point: NaI-like model on the paper's grid, implicit midpoint
+# composed by Suzuki's fractal to order 8 with dt = t_f / 1024 (t_f = 10500
+# a.u.), implicit steps solved to tol 1e-15: the convergence sweeps
+# (--sweep) put the error ||psi_dt(t_f) - psi_dt/2(t_f)|| of this point at
+# the 1e-10 level; looser solves add an accumulated error of the same size.
+WORKLOAD = dict(name="nai_like_n2048_s2_midpoint_suzuki8_dt10.25au", N=2048, S=2, method=1, order=8, scheme=1,
+                dt_fs=10500.0 / 1024 / FS, tol=1e-15, restart=30)
 
 
 def _flops_per_launch(stats, N, S, reorth=True, mixed=False):
@@ -171,7 +172,8 @@ def run_ours(args):
     prec = qg.QG_C64_MIXED if args.precision == "mixed" else qg.QG_C128
     grid, model, states = _setup_batch(qg, wl, B, rank, stream.cuda_stream, prec)
     batch = qg.Batch(states)
-    opts = qg.default_solver_opts(tol=WORKLOAD["tol"], restart=WORKLOAD["restart"])
+    opts = qg.default_solver_opts(tol=WORKLOAD["tol"], restart=WORKLOAD["restart"], max_iters=600,
+                                  solver=qg.QG_SOLVER_LANCZOS if args.solver == "lanczos" else qg.QG_SOLVER_GMRES)
     dt = WORKLOAD["dt_fs"] * FS
     m, o, sc = WORKLOAD["method"], WORKLOAD["order"], WORKLOAD["scheme"]
     N, S = WORKLOAD["N"], WORKLOAD["S"]
@@ -250,7 +252,7 @@ def run_ours(args):
                        "method": "implicit midpoint" if m == 1 else "trapezoidal",
                        "order": o, "scheme": "suzuki" if sc == 1 else "triple_jump",
                        "dt_fs": WORKLOAD["dt_fs"], "gmres_tol": WORKLOAD["tol"], "restart": WORKLOAD["restart"],
-                       "precision": args.precision,
+                       "precision": args.precision, "solver": args.solver,
                        "l2": "working set %.0f MB > L2 (129 MB): no flush needed" %
                              (B * (WORKLOAD["restart"] + 6) * len_state * 16 / 1e6)},
             "hpsi_grid_point_applications_per_s": hpsi_rate,
@@ -353,6 +355,284 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+BATCHED = dict(name="avoided_crossing_x4096_midpoint_suzuki4", models=4096, seed0=1000, method=1, order=4,
+               scheme=1, dt_fs=0.1, tol=1e-12, restart=30)
+
+
+def run_batched(args):
+    """Batched workload: independent seeded avoided-crossing models (S = 2-3,
+    N = 256..8192 log-uniform), all propagated by one persistent launch per
+    composed step, replayed from a CUDA graph.  Also times the per-instance
+    path (one launch per model) on a sample of the same models."""
+    import torch
+    import __graft_entry__
+    import workloads as wl
+
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    import paper_1902_04661_gb300 as qg
+
+    nmod = args.models or BATCHED["models"]
+    prec = qg.QG_C64_MIXED if args.precision == "mixed" else qg.QG_C128
+    stream = torch.cuda.current_stream()
+    keep, states, sizes = [], [], []
+    for i in range(nmod):
+        m = wl.avoided_crossing_model(BATCHED["seed0"] + i)
+        g = qg.Grid([m["N"]], [m["qmin"]], [m["qmax"]])
+        lm = qg.Model(g, m["S"], [m["mass"]], W=m["W"], dW=m["dW"])
+        st = qg.State(lm, precision=prec, stream=stream.cuda_stream)
+        st.set_gaussian(m["surface"], [m["q0"]], [m["p0"]], [m["sigma0"]])
+        keep += [g, lm]
+        states.append(st)
+        sizes.append((m["N"], m["S"]))
+    batch = qg.Batch(states)
+    opts = qg.default_solver_opts(tol=BATCHED["tol"], restart=BATCHED["restart"])
+    dt = BATCHED["dt_fs"] * FS
+    m_, o_, s_ = BATCHED["method"], BATCHED["order"], BATCHED["scheme"]
+    tuning = batch.autotune(m_, o_, s_, dt, 1, opts)
+    batch.capture(m_, o_, s_, dt, 1, opts)
+    bstream = torch.cuda.ExternalStream(batch.stream)
+    for _ in range(args.warmup):
+        batch.replay()
+    batch.stats()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    stats_all = []
+    with ClockSampler(0) as clk:
+        ev[0].record(bstream)
+        for k in range(args.steps):
+            batch.replay()
+            ev[k + 1].record(bstream)
+        torch.cuda.synchronize()
+        stt, st_ = batch.stats()
+    t_ms = ev[0].elapsed_time(ev[args.steps])
+    # every replay ran the same step; the statistics of the last one stand for each
+    hpsi_pts = sum(s["n_hpsi"] * n * S for s, (n, S) in zip(st_, sizes))
+    value = nmod * args.steps / (t_ms / 1e3)
+    # per-instance path: one qg_propagate launch per model, on a sample
+    ns = min(nmod, args.per_instance_sample)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for st in states[:ns]:
+        st.propagate(m_, o_, s_, dt, 1, opts)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    per_ms = t0.elapsed_time(t1)
+    per_value = ns / (per_ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": "wavepacket-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == qg.QG_C128 else "c64 inner / f64 residual",
+            "data": "synthetic (seeded avoided-crossing models)",
+            "config": {"workload": BATCHED["name"], "models": nmod, "S": "2-3", "N": "256-8192 log-uniform",
+                       "method": "implicit midpoint", "order": o_, "scheme": "suzuki", "dt_fs": BATCHED["dt_fs"],
+                       "gmres_tol": BATCHED["tol"], "precision": args.precision,
+                       "launch": "one persistent launch per step, CUDA graph replay"},
+            "hpsi_grid_point_applications_per_s": hpsi_pts * args.steps / (t_ms / 1e3),
+            "per_instance_path": {"value": per_value, "unit": "wavepacket-steps/s", "sample_models": ns,
+                                  "speedup_of_batched": value / per_value},
+            "gpu_launches": args.steps, "clocks": clk.summary(), "autotune": tuning,
+            "statuses_ok": sum(1 for x in stt if x == 0)}
+    print(json.dumps(line), flush=True)
+
+
+SWEEP_JOBS = {
+    # (scheme, order): step counts n (dt = t_f / n) to run; each error uses n and 2n
+    (1, 2): [1024, 2048, 4096, 8192, 16384, 32768],
+    (0, 4): [512, 1024, 2048, 4096, 8192],
+    (1, 4): [256, 512, 1024, 2048, 4096],
+    (0, 6): [256, 512, 1024, 2048],
+    (1, 6): [128, 256, 512, 1024],
+    (0, 8): [128, 256],
+    (1, 8): [64, 128, 256],
+}
+
+
+def run_2d(args):
+    """2-D two-surface model, 256 x 256 grid, Suzuki order 6, one instance over
+    the whole GPU (cooperative launch): complex64-inner / FP64-refined form
+    timed against the plain FP64 path on the same steps, with the difference
+    between the two results."""
+    import torch
+    import __graft_entry__
+    import workloads as wl
+
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    import paper_1902_04661_gb300 as qg
+
+    p = wl.MODEL2D_PARAMS
+    ns = (256, 256)
+    q1 = p["qmin"][0] + (p["qmax"][0] - p["qmin"][0]) / ns[0] * np.arange(ns[0])
+    q2 = p["qmin"][1] + (p["qmax"][1] - p["qmin"][1]) / ns[1] * np.arange(ns[1])
+    W, dW = wl.model2d_diabatic(q1, q2, p)
+    g = qg.Grid(list(ns), list(p["qmin"]), list(p["qmax"]))
+    m = qg.Model(g, 2, list(p["mass"]), W=W, dW=dW)
+    q0, p0, s0 = wl.model2d_initial()
+    dt = 0.1 * FS
+    opts = qg.default_solver_opts(tol=1e-12)
+    res = {}
+    for name, prec in (("mixed", qg.QG_C64_MIXED), ("fp64", qg.QG_C128)):
+        st = qg.State(m, precision=prec)
+        st.set_gaussian(1, q0, p0, s0)
+        for _ in range(args.warmup):
+            st.propagate(1, 6, 1, dt, 1, opts)
+        st.set_gaussian(1, q0, p0, s0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        s_ = st.propagate(1, 6, 1, dt, args.steps, opts)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = dict(ms=e0.elapsed_time(e1), stats=s_, psi=st.get(), norm=st.norm())
+    dv = np.prod([(p["qmax"][d] - p["qmin"][d]) / ns[d] for d in range(2)])
+    err = float(np.linalg.norm(res["mixed"]["psi"] - res["fp64"]["psi"]) * np.sqrt(dv))
+    t_m, t_f = res["mixed"]["ms"], res["fp64"]["ms"]
+    line = {"metric": METRIC, "value": args.steps / (t_m / 1e3), "unit": "wavepacket-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_m / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "c64 inner / f64 residual",
+            "data": "synthetic (2-D two-state model)",
+            "config": {"workload": "model2d_256x256_midpoint_suzuki6", "grid": list(ns), "S": 2, "order": 6,
+                       "dt_fs": 0.1, "gmres_tol": 1e-12, "launch": "one cooperative launch over all SMs"},
+            "fp64_path": {"value": args.steps / (t_f / 1e3), "ms_per_step": t_f / args.steps,
+                          "fp64_hpsi": res["fp64"]["stats"]["n_hpsi"]},
+            "speedup_mixed_over_fp64": t_f / t_m,
+            "mixed_vs_fp64_l2": err, "norm_drift": abs(res["mixed"]["norm"] - 1.0),
+            "mixed_hpsi": {"fp64": res["mixed"]["stats"]["n_hpsi"], "c64": res["mixed"]["stats"]["n_hpsi32"]},
+            "hpsi_grid_point_applications_per_s":
+                (res["mixed"]["stats"]["n_hpsi"] + res["mixed"]["stats"]["n_hpsi32"]) * ns[0] * ns[1] / (t_m / 1e3)}
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args):
+    """Gradients of the final excited-state population of seeded NaI-like
+    models (8 diabatic parameters perturbed by up to 5 %) by the adjoint form:
+    one batched checkpointed forward launch and one batched adjoint launch."""
+    import torch
+    import __graft_entry__
+    import workloads as wl
+
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    import paper_1902_04661_gb300 as qg
+    from paper_1902_04661_gb300 import autograd as qad
+
+    nm = args.models or 256
+    N = WORKLOAD["N"]
+    g = qg.Grid([N], [wl.NAI_QMIN], [wl.NAI_QMAX])
+    q = g.points()
+    base = wl.nai_like_params()
+    keys = ["E_ion", "A_ion", "rho_ion", "B_cov", "rho_cov", "A_c", "beta_c", "q_c"]
+    Vs, Fs = [], []
+    for i in range(nm):
+        rng = np.random.default_rng(5000 + i)
+        par = dict(base)
+        for k in keys:
+            par[k] = base[k] * (1 + 0.05 * rng.uniform(-1, 1))
+        W, dW = wl.nai_like_diabatic(q, par)
+        V, F = qg.Model(g, 2, [wl.NAI_REDUCED_MASS], W=W, dW=dW).fields()
+        Vs.append(V)
+        Fs.append(F[0])
+    V = torch.tensor(np.stack(Vs), device="cuda", requires_grad=True)
+    F = torch.tensor(np.stack(Fs), device="cuda", requires_grad=True)
+    st = qg.State(qg.Model(g, 2, [wl.NAI_REDUCED_MASS], V=Vs[0], F=Fs[0][None]))
+    st.set_gaussian(1, [wl.NAI_Q0], [0.0], [wl.NAI_SIGMA0])
+    psi0 = torch.tensor(np.stack([st.get()] * nm), device="cuda", requires_grad=True)
+    dt, nsteps = 0.5 * FS, args.steps
+    opts = qg.default_solver_opts(tol=1e-12)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    out = qad.propagate_batch(V, F, psi0, g, wl.NAI_REDUCED_MASS, 1, 4, 1, dt, nsteps, 8, opts)
+    e1.record()
+    L = (g.dq[0] * (out[:, 1].abs() ** 2)).sum()
+    L.backward()
+    e2.record()
+    torch.cuda.synchronize()
+    tf, tb = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    line = {"metric": METRIC, "value": nm * nsteps / ((tf + tb) / 1e3), "unit": "wavepacket-steps/s (forward+adjoint)",
+            "n_gpus": 1, "steps": nsteps, "warmup": 0, "ms_per_step": (tf + tb) / nsteps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (perturbed NaI-like models)",
+            "config": {"workload": "nai_like_adjoint_x%d_n2048_suzuki4" % nm, "models": nm, "N": N, "order": 4,
+                       "dt_fs": 0.5, "checkpoint_every": 8},
+            "forward_ms": tf, "adjoint_ms": tb, "adjoint_over_forward": tb / tf,
+            "grad_norms": {"V": float(V.grad.norm()), "F": float(F.grad.norm()), "psi0": float(psi0.grad.norm())}}
+    print(json.dumps(line), flush=True)
+
+
+# the cheapest point of the coarse sweep, refined: Suzuki order 8 around
+# dt = t_f / 1024
+SWEEP_VERIFY = {(1, 8): [768, 1024, 1536, 2048]}
+
+
+def run_sweep(args):
+    """Convergence error ||psi_dt(t_f) - psi_dt/2(t_f)|| (Sec. III, Fig. 3) of the
+    NaI-like workload for every (scheme, order, dt = t_f / n) in SWEEP_JOBS,
+    each propagation one CTA on its own stream, all concurrent.  Prints one
+    JSON line per finished propagation (wall time, H psi count) as it
+    completes, then one line per (scheme, order, dt) with the error."""
+    import concurrent.futures as cf
+    import torch
+    import __graft_entry__
+    import workloads as wl
+
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    import paper_1902_04661_gb300 as qg
+
+    N = WORKLOAD["N"]
+    tf = args.tf
+    grid = qg.Grid([N], [wl.NAI_QMIN], [wl.NAI_QMAX])
+    W, dW = wl.nai_like_diabatic(grid.points())
+    model = qg.Model(grid, 2, [wl.NAI_REDUCED_MASS], W=W, dW=dW)
+    prec = qg.QG_C64_MIXED if args.precision == "mixed" else qg.QG_C128
+    table = SWEEP_VERIFY if args.sweep_set == "verify" else SWEEP_JOBS
+    jobs = [(sc, o, n) for (sc, o), ns in table.items() for n in ns]
+    jobs.sort(key=lambda j: -j[2] * (3 if j[0] == 0 else 5) ** (j[1] // 2 - 1))
+    opts = qg.default_solver_opts(tol=args.sweep_tol, max_iters=600,
+                                  solver=qg.QG_SOLVER_LANCZOS if args.solver == "lanczos" else qg.QG_SOLVER_GMRES)
+    outdir = args.sweep_dir
+    if outdir:
+        os.makedirs(outdir, exist_ok=True)
+
+    def one(job):
+        scheme, order, n = job
+        stream = torch.cuda.Stream()
+        st = qg.State(model, precision=prec, stream=stream)
+        st.set_gaussian(1, [wl.NAI_Q0], [wl.NAI_P0], [wl.NAI_SIGMA0])
+        t0 = time.perf_counter()
+        stats = st.propagate(WORKLOAD["method"], order, scheme, tf / n, n, opts, allow_fail=True)
+        el = time.perf_counter() - t0
+        psi = st.get()
+        row = {"scheme": "suzuki" if scheme == 1 else "triple_jump", "order": order, "nsteps": n, "dt_au": tf / n,
+               "dt_fs": tf / n / FS, "status": stats["status"], "wall_s": el, "hpsi": stats["n_hpsi"],
+               "substeps": stats["n_substeps"], "krylov_per_substep": stats["n_krylov"] / max(1, stats["n_substeps"])}
+        print(json.dumps(row), flush=True)
+        if outdir:
+            np.save(os.path.join(outdir, "psi_%d_%d_%d.npy" % job), psi)
+        return job, psi, row
+
+    with cf.ThreadPoolExecutor(len(jobs)) as ex:
+        res = list(ex.map(one, jobs))
+    byk = {j: (psi, row) for j, psi, row in res}
+    dq = grid.dq[0]
+    best = None
+    for (scheme, order, n), (psi, row) in sorted(byk.items()):
+        nxt = byk.get((scheme, order, 2 * n))
+        if nxt is None or row["status"] != 0 or nxt[1]["status"] != 0:
+            continue
+        err = float(np.linalg.norm(psi - nxt[0]) * np.sqrt(dq))
+        row = dict(row, error=err)
+        print(json.dumps({"error_row": row}), flush=True)
+        if err <= 1e-10 and (best is None or row["wall_s"] < best["wall_s"]):
+            best = row
+    print(json.dumps({"sweep_best_at_1e-10": best, "t_f": tf, "tol": args.sweep_tol,
+                      "precision": args.precision}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,10 +642,27 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="wavepackets per GPU (default: one per SM)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="convergence-error sweep that fixes the operating point")
+    ap.add_argument("--solver", default="gmres", choices=["gmres", "lanczos"])
+    ap.add_argument("--workload", default="nai", choices=["nai", "batched", "2d", "adjoint"])
+    ap.add_argument("--models", type=int, default=0)
+    ap.add_argument("--per-instance-sample", type=int, default=64)
+    ap.add_argument("--tf", type=float, default=10500.0)
+    ap.add_argument("--sweep-tol", type=float, default=1e-15)
+    ap.add_argument("--sweep-dir", default="")
+    ap.add_argument("--sweep-set", default="verify", choices=["verify", "coarse"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every Krylov iteration in FP64; mixed: complex64 inner solves, FP64 refinement")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args)
+    elif args.workload == "batched" and args.impl == "ours":
+        run_batched(args)
+    elif args.workload == "2d" and args.impl == "ours":
+        run_2d(args)
+    elif args.workload == "adjoint" and args.impl == "ours":
+        run_adjoint(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -103,7 +103,12 @@ typedef struct qg_batch* qg_batch_t;
  * inner_tol: QG_C64_MIXED only -- relative tolerance of each complex64 inner
  *      solve, default 1e-6.
  * max_outer: QG_C64_MIXED only -- cap on FP64 refinement steps per implicit
- *      solve, default 10; exceeding it is QG_ERR_NOT_CONVERGED. */
+ *      solve, default 10; exceeding it is QG_ERR_NOT_CONVERGED.
+ * solver: QG_SOLVER_GMRES (default; restarted GMRES with Arnoldi/CGS as in
+ *      Sec. II B) or QG_SOLVER_LANCZOS (the same minimal-residual iterates by
+ *      the three-term recurrence that the Hermitian H allows: 5 work vectors,
+ *      O(1) vector passes per iteration; needs restart >= 4). */
+enum { QG_SOLVER_GMRES = 0, QG_SOLVER_LANCZOS = 1 };
 typedef struct {
   double tol;
   int restart;
@@ -113,6 +118,7 @@ typedef struct {
   int true_residual;
   double inner_tol;
   int max_outer;
+  int solver;
 } qg_solver_opts;
 
 /* Statistics of one propagate / step call (summed over all sub-steps). */
@@ -150,13 +156,16 @@ void qg_destroy_grid(qg_grid_t g);
 qg_status qg_create_model(qg_grid_t g, int S, const double* mass, const double* V,
                           const double* F, int on_device, qg_model_t* out);
 
-/* Adiabatic model from a two-state diabatic matrix W(q) and its derivative
- * (Sec. II E): V_{1,2} = Wbar +- sqrt((dW/2)^2 + W12^2) (Eq. pot_diab2adiab
- * with the orthogonal matrix of Eq. ..._orthogonal_transformation) and the
- * coupling of Eq. (nonadiab_c), computed on the device per grid point.  The
- * paper labels the upper surface 1; this library stores surfaces ascending,
+/* Adiabatic model from a diabatic matrix W(q) and its derivative (Sec. II E),
+ * computed on the device per grid point.  S = 2: V_{1,2} = Wbar +-
+ * sqrt((dW/2)^2 + W12^2) (Eq. pot_diab2adiab with the orthogonal matrix of
+ * Eq. ..._orthogonal_transformation) and the coupling of Eq. (nonadiab_c); the
+ * paper labels the upper surface 1, this library stores surfaces ascending,
  * so V[0] is the ground and F[0] = F_{ground,excited} = -F_12 (paper).
- * S must be 2. */
+ * S = 3, 4: the same definitions V = O^T W O, F = O^T O' taken numerically:
+ * Jacobi eigen-decomposition per point (ascending), F_ij = <phi_i|W'|phi_j> /
+ * (V_j - V_i), eigenvector signs fixed by continuity along the grid (largest
+ * component positive at the first point).  Only D = 1 grids. */
 qg_status qg_create_model_diabatic(qg_grid_t g, int S, const double* mass, const double* W,
                                    const double* dW, int on_device, qg_model_t* out);
 /* Copy the model's V and F (layouts above) to host (on_device = 0) or device
@@ -192,6 +201,36 @@ qg_status qg_step_implicit(qg_state_t s, int method, int order, int scheme, doub
 qg_status qg_propagate(qg_state_t s, int method, int order, int scheme, double dt,
                        int64_t nsteps, const qg_solver_opts* opts, qg_step_stats* stats);
 
+/* Reverse-mode differentiation through a propagation (not in the paper; it
+ * relies on the unitarity and exact time reversibility of the composed
+ * Cayley maps, Sec. II A-C).
+ * qg_state_set_adjoint attaches caller-owned device buffers to a state:
+ *   checkpoints: ncheckpoints vectors of S*N complex128 (may be NULL);
+ *   every: composed steps between checkpoints (>= 1);
+ *   grad: S*N complex128, dL/dpsi at the final time on entry to an adjoint
+ *         run, dL/dpsi(0) on exit (torch convention dL = Re sum conj(g) dpsi);
+ *   grad_V: S*N doubles and grad_F: S(S-1)/2*N doubles, ACCUMULATED (+=)
+ *         with dL/dV_s(q_j) and dL/dF_ab(q_j) (upper-triangle layout).
+ * Attach before qg_batch_create when the state is used in a batch.
+ * Run kinds for qg_propagate_ex / qg_batch_run_ex:
+ *   QG_RUN_FORWARD     plain propagation (= qg_propagate);
+ *   QG_RUN_CHECKPOINT  propagation that stores psi before every `every`-th
+ *                      composed step into the checkpoints;
+ *   QG_RUN_ADJOINT     from psi(t_f) (the state) and grad, steps backward
+ *                      nsteps composed steps: psi is re-propagated with
+ *                      U(-dt) and reset to the stored checkpoints, the
+ *                      adjoint is propagated with U^dagger = U(-dt), and the
+ *                      field gradients are accumulated; on exit the state is
+ *                      psi(0) and grad is dL/dpsi(0).  FP64 solves; restart
+ *                      must be <= 60. */
+enum { QG_RUN_FORWARD = 0, QG_RUN_CHECKPOINT = 1, QG_RUN_ADJOINT = 2 };
+qg_status qg_state_set_adjoint(qg_state_t s, void* checkpoints, int64_t ncheckpoints, int64_t every, void* grad,
+                               double* grad_V, double* grad_F);
+qg_status qg_propagate_ex(qg_state_t s, int run, int method, int order, int scheme, double dt, int64_t nsteps,
+                          const qg_solver_opts* opts, qg_step_stats* stats);
+qg_status qg_batch_run_ex(qg_batch_t b, int run, int method, int order, int scheme, double dt, int64_t nsteps,
+                          const qg_solver_opts* opts, int32_t* statuses, qg_step_stats* stats);
+
 /* Observables (Sec. II A): norm ||psi||, energy <psi|H|psi>, populations
  * P_s = ||psi_s||^2 (out: S doubles), overlap <a|b> (out: {re, im}).
  * Results are written to host memory; the call synchronises the stream. */
@@ -215,9 +254,33 @@ qg_status qg_batch_propagate(qg_state_t* states, int nstates, int method, int or
  * qg_batch_run calls allocate nothing.  The states must outlive the batch
  * and keep their models; the stream of states[0] is used. */
 qg_status qg_batch_create(qg_state_t* states, int nstates, qg_batch_t* out);
-/* Same semantics as qg_batch_propagate on the batch's states. */
+/* Same semantics as qg_batch_propagate on the batch's states.  The batch
+ * hands instances to the persistent CTAs longest estimated work first. */
 qg_status qg_batch_run(qg_batch_t b, int method, int order, int scheme, double dt, int64_t nsteps,
                        const qg_solver_opts* opts, int32_t* statuses, qg_step_stats* stats);
+/* Capture one batch run (the work-counter reset and the single persistent
+ * launch of nsteps composed steps) as a CUDA graph, replayed by
+ * qg_batch_replay (asynchronous, in the batch's stream); qg_batch_stats then
+ * copies the statuses and statistics of the last run to the host
+ * (synchronises; same return convention as qg_batch_run).  When the states'
+ * stream is the legacy default stream the batch uses a private stream,
+ * returned by qg_batch_stream. */
+qg_status qg_batch_capture(qg_batch_t b, int method, int order, int scheme, double dt, int64_t nsteps,
+                           const qg_solver_opts* opts);
+qg_status qg_batch_replay(qg_batch_t b);
+/* Autotuner of the batched launch (not in the paper): times trial_steps
+ * composed steps of the real batch under each candidate launch shape --
+ * {1, 2} CTAs per SM x {all surfaces of an instance per shared-memory FFT
+ * batch, one surface at a time} -- restoring every state after each trial,
+ * and keeps the fastest for later qg_batch_run / qg_batch_capture calls (a
+ * captured graph is dropped).  ms_out (4 doubles, may be NULL) receives the
+ * trial times in that order, -1 for a shape that does not fit.
+ * qg_batch_tuning reports the chosen shape (surfaces_per_fft 0 = all). */
+qg_status qg_batch_autotune(qg_batch_t b, int method, int order, int scheme, double dt, int64_t trial_steps,
+                            const qg_solver_opts* opts, double* ms_out);
+qg_status qg_batch_tuning(qg_batch_t b, int* ctas_per_sm, int* surfaces_per_fft);
+qg_status qg_batch_stats(qg_batch_t b, int32_t* statuses, qg_step_stats* stats);
+void* qg_batch_stream(qg_batch_t b);
 void qg_batch_destroy(qg_batch_t b);
 
 /* Propagation without any device allocation.  The paper has no counterpart:

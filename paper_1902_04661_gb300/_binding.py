@@ -29,6 +29,11 @@ QG_TRIPLE_JUMP = 0
 QG_SUZUKI = 1
 QG_C128 = 0
 QG_C64_MIXED = 1
+QG_SOLVER_GMRES = 0
+QG_SOLVER_LANCZOS = 1
+QG_RUN_FORWARD = 0
+QG_RUN_CHECKPOINT = 1
+QG_RUN_ADJOINT = 2
 
 # Every symbol declared in include/qgeom.h.
 EXPORTED = [
@@ -36,7 +41,8 @@ EXPORTED = [
     "qg_create_model_diabatic", "qg_model_fields", "qg_destroy_model", "qg_create_state",
     "qg_destroy_state", "qg_state_set_stream", "qg_set_state", "qg_get_state", "qg_set_gaussian",
     "qg_apply_h", "qg_step_implicit", "qg_propagate", "qg_norm", "qg_energy", "qg_population",
-    "qg_overlap", "qg_batch_propagate", "qg_batch_create", "qg_batch_run", "qg_batch_destroy", "qg_propagate_noalloc", "qg_status_string", "qg_last_error_string", "qg_version",
+    "qg_overlap", "qg_batch_propagate", "qg_batch_create", "qg_batch_run", "qg_batch_capture", "qg_batch_replay", "qg_batch_stats",
+    "qg_batch_stream", "qg_batch_destroy", "qg_batch_autotune", "qg_batch_tuning", "qg_state_set_adjoint", "qg_propagate_ex", "qg_batch_run_ex", "qg_propagate_noalloc", "qg_status_string", "qg_last_error_string", "qg_version",
 ]
 
 
@@ -53,7 +59,7 @@ class QgError(RuntimeError):
 class SolverOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("reorth", ctypes.c_int), ("midpoint_epilogue", ctypes.c_int), ("true_residual", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("solver", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -106,7 +112,19 @@ def lib():
             "qg_batch_create": (I, [ctypes.POINTER(P), I, PP]),
             "qg_batch_run": (I, [P, I, I, I, D, ctypes.c_int64, ctypes.POINTER(SolverOpts),
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(StepStats)]),
+            "qg_batch_capture": (I, [P, I, I, I, D, ctypes.c_int64, ctypes.POINTER(SolverOpts)]),
+            "qg_batch_replay": (I, [P]),
+            "qg_batch_stats": (I, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(StepStats)]),
+            "qg_batch_stream": (P, [P]),
+            "qg_batch_autotune": (I, [P, I, I, I, D, ctypes.c_int64, ctypes.POINTER(SolverOpts),
+                                      ctypes.POINTER(ctypes.c_double)]),
+            "qg_batch_tuning": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
             "qg_batch_destroy": (V, [P]),
+            "qg_state_set_adjoint": (I, [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P]),
+            "qg_propagate_ex": (I, [P, I, I, I, I, D, ctypes.c_int64, ctypes.POINTER(SolverOpts),
+                                    ctypes.POINTER(StepStats)]),
+            "qg_batch_run_ex": (I, [P, I, I, I, I, D, ctypes.c_int64, ctypes.POINTER(SolverOpts),
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(StepStats)]),
             "qg_propagate_noalloc": (I, [I, D, D, I, D, P, P, P, I, I, I, D, ctypes.c_int64,
                                          ctypes.POINTER(SolverOpts), ctypes.POINTER(StepStats), P]),
             "qg_status_string": (ctypes.c_char_p, [I]),
@@ -350,6 +368,34 @@ class Batch:
         if not want_stats:
             return None
         return list(self._stt), [s.as_dict() for s in self._sts]
+
+    def capture(self, method, order, scheme, dt, nsteps, opts=None):
+        o = opts if opts is not None else default_solver_opts()
+        _check(lib().qg_batch_capture(self.handle, method, order, scheme, float(dt), int(nsteps), ctypes.byref(o)),
+               "qg_batch_capture")
+
+    def replay(self):
+        _check(lib().qg_batch_replay(self.handle), "qg_batch_replay")
+
+    def stats(self, allow_fail=False):
+        r = lib().qg_batch_stats(self.handle, self._stt, self._sts)
+        _check(r, "qg_batch_stats", allow=(QG_ERR_NOT_CONVERGED,) if allow_fail else ())
+        return list(self._stt), [s.as_dict() for s in self._sts]
+
+    def autotune(self, method, order, scheme, dt, trial_steps=1, opts=None):
+        """Pick the fastest launch shape on the real batch; returns the trial
+        times (ms) of {1, 2} CTAs/SM x {all surfaces, one surface} per FFT."""
+        o = opts if opts is not None else default_solver_opts()
+        ms = (ctypes.c_double * 4)()
+        _check(lib().qg_batch_autotune(self.handle, method, order, scheme, float(dt), int(trial_steps),
+                                       ctypes.byref(o), ms), "qg_batch_autotune")
+        c, s = ctypes.c_int(), ctypes.c_int()
+        _check(lib().qg_batch_tuning(self.handle, ctypes.byref(c), ctypes.byref(s)), "qg_batch_tuning")
+        return {"trial_ms": list(ms), "ctas_per_sm": c.value, "surfaces_per_fft": s.value}
+
+    @property
+    def stream(self):
+        return lib().qg_batch_stream(self.handle)
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "qg_internal.h"
@@ -117,13 +118,15 @@ void default_opts(qg_solver_opts* o) {
   o->true_residual = 0;
   o->inner_tol = 1e-6;
   o->max_outer = 10;
+  o->solver = QG_SOLVER_GMRES;
 }
 
 bool valid_opts(const qg_solver_opts& o) {
   return o.tol > 0.0 && o.restart >= 1 && o.restart <= QG_MAX_RESTART && o.max_iters >= 1 &&
          (o.reorth == 0 || o.reorth == 1) && (o.midpoint_epilogue == 0 || o.midpoint_epilogue == 1) &&
          (o.true_residual == 0 || o.true_residual == 1) && o.inner_tol > 0.0 && o.inner_tol < 1.0 &&
-         o.max_outer >= 1 && o.max_outer <= 1000;
+         o.max_outer >= 1 && o.max_outer <= 1000 &&
+         (o.solver == QG_SOLVER_GMRES || (o.solver == QG_SOLVER_LANCZOS && o.restart >= 4));
 }
 
 // Composition fractions (Sec. II C): order 2 is the elementary step; each
@@ -175,7 +178,54 @@ InstDesc make_desc(const qg_state* s) {
   d.V32 = m->d_V32;
   d.F32 = m->d_F32;
   d.work32 = s->d_work32;
+  d.ckpt = s->adj.ckpt;
+  d.nckpt = s->adj.nckpt;
+  d.every = s->adj.every > 0 ? s->adj.every : 1;
+  d.grad = s->adj.grad;
+  d.gV = s->adj.gV;
+  d.gF = s->adj.gF;
   return d;
+}
+
+Inst2D make_inst2d(const qg_state* s) {
+  const qg_model* m = s->m;
+  const qg_grid* g = m->g;
+  Inst2D I;
+  memset(&I, 0, sizeof(I));
+  I.S = m->S;
+  I.dv = 1.0;
+  for (int d = 0; d < 2; ++d) {
+    I.n[d] = g->n[d];
+    I.npass[d] = g->plan[d].npass;
+    for (int i = 0; i < QG_MAX_PASSES; ++i) I.radix[d][i] = g->plan[d].radix[i];
+    I.h2m[d] = 1.0 / (2.0 * m->mass[d]);
+    I.dv *= g->dq[d];
+    I.tw[d] = g->d_tw[d];
+    I.kd[d] = g->d_kd[d];
+    I.tw32[d] = g->d_tw32[d];
+    I.kd32[d] = g->d_kd32[d];
+  }
+  I.V = m->d_V;
+  I.F = m->d_F;
+  I.V32 = m->d_V32;
+  I.F32 = m->d_F32;
+  I.psi = s->d_psi;
+  I.work = s->d_work;
+  I.work32 = s->d_work32;
+  I.precision = s->precision;
+  I.bar = reinterpret_cast<unsigned*>(s->d_coop);
+  I.err = reinterpret_cast<int*>(s->d_coop + 64);
+  I.gred = reinterpret_cast<double*>(s->d_coop + 4096);
+  I.ckpt = s->adj.ckpt;
+  I.nckpt = s->adj.nckpt;
+  I.every = s->adj.every > 0 ? s->adj.every : 1;
+  return I;
+}
+
+double grid_dv(const qg_grid* g) {
+  double v = 1.0;
+  for (int d = 0; d < g->D; ++d) v *= g->dq[d];
+  return v;
 }
 
 }  // namespace
@@ -212,11 +262,14 @@ const char* qg_status_string(qg_status st) {
 qg_status qg_create_grid(int D, const int* N, const double* qmin, const double* qmax, qg_grid_t* out) {
   if (!out || !N || !qmin || !qmax) return QG_ERR_INVALID_ARG;
   *out = nullptr;
-  if (D < 1 || D > QG_MAX_D) return D == 2 ? QG_ERR_UNSUPPORTED : QG_ERR_INVALID_ARG;
+  if (D < 1 || D > QG_MAX_D) return QG_ERR_INVALID_ARG;
+  long long tot = 1;
   for (int d = 0; d < D; ++d) {
     if (!is_pow2(N[d]) || N[d] < QG_MIN_N || N[d] > QG_MAX_N) return QG_ERR_INVALID_ARG;
     if (!(qmax[d] > qmin[d]) || !std::isfinite(qmin[d]) || !std::isfinite(qmax[d])) return QG_ERR_INVALID_ARG;
+    tot *= N[d];
   }
+  if (D == 2 && tot > QG_MAX_2D_POINTS) return QG_ERR_INVALID_ARG;
   qg_grid* g = new (std::nothrow) qg_grid;
   if (!g) return QG_ERR_OOM;
   memset(g, 0, sizeof(*g));
@@ -336,25 +389,36 @@ qg_status qg_create_model(qg_grid_t g, int S, const double* mass, const double* 
 qg_status qg_create_model_diabatic(qg_grid_t g, int S, const double* mass, const double* W, const double* dW,
                                    int on_device, qg_model_t* out) {
   if (!out || !W || !dW) return QG_ERR_INVALID_ARG;
-  if (S != 2) return QG_ERR_UNSUPPORTED;
+  if (g && g->D != 1 && S != 2) return QG_ERR_UNSUPPORTED;
   qg_model* m;
   qg_status st = alloc_model(g, S, mass, &m);
   if (st != QG_OK) return st;
   const int n = g->ntot;
-  double *dWd = nullptr, *ddW = nullptr;
+  const size_t nw = (size_t)(S * (S + 1) / 2) * n;
+  const size_t ndw = nw * g->D;
+  double *dWd = nullptr, *ddW = nullptr, *dvec = nullptr;
   cudaError_t e = cudaSuccess;
   if (!on_device) {
-    e = cudaMalloc(&dWd, sizeof(double) * 3 * n);
-    if (e == cudaSuccess) e = cudaMalloc(&ddW, sizeof(double) * 3 * n);
-    if (e == cudaSuccess) e = cudaMemcpy(dWd, W, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(ddW, dW, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+    e = cudaMalloc(&dWd, sizeof(double) * nw);
+    if (e == cudaSuccess) e = cudaMalloc(&ddW, sizeof(double) * ndw);
+    if (e == cudaSuccess) e = cudaMemcpy(dWd, W, sizeof(double) * nw, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ddW, dW, sizeof(double) * ndw, cudaMemcpyHostToDevice);
   }
-  if (e == cudaSuccess)
-    e = qg_launch_fields2(on_device ? W : dWd, on_device ? dW : ddW, n, m->d_V, m->d_F, 0);
+  const double* w = on_device ? W : dWd;
+  const double* dw = on_device ? dW : ddW;
+  if (e == cudaSuccess) {
+    if (S == 2) {
+      e = qg_launch_fields2(w, dw, n, g->D, m->d_V, m->d_F, 0);
+    } else {
+      e = cudaMalloc(&dvec, sizeof(double) * (size_t)S * S * n);
+      if (e == cudaSuccess) e = qg_launch_fieldsS(w, dw, n, S, m->d_V, m->d_F, dvec, 0);
+    }
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = finish_model(m);
   if (dWd) cudaFree(dWd);
   if (ddW) cudaFree(ddW);
+  if (dvec) cudaFree(dvec);
   if (e != cudaSuccess) {
     set_err("qg_create_model_diabatic", e);
     qg_destroy_model(m);
@@ -402,6 +466,7 @@ qg_status qg_create_state(qg_model_t m, int precision, qg_state_t* out) {
     e = cudaMalloc(&s->d_work32, sizeof(float2) * len * (size_t)(s->restart_cap + 4));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_stats, sizeof(qg_step_stats));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_scalars, sizeof(double) * 64);
+  if (e == cudaSuccess && m->g->D == 2) e = cudaMalloc(&s->d_coop, 4096 + sizeof(double) * 2 * 1024 * 32);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_inst, sizeof(InstDesc));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, sizeof(int));
   if (e != cudaSuccess) {
@@ -430,6 +495,7 @@ void qg_destroy_state(qg_state_t s) {
   if (s->d_psi) cudaFree(s->d_psi);
   if (s->d_work) cudaFree(s->d_work);
   if (s->d_work32) cudaFree(s->d_work32);
+  if (s->d_coop) cudaFree(s->d_coop);
   if (s->d_stats) cudaFree(s->d_stats);
   if (s->d_scalars) cudaFree(s->d_scalars);
   if (s->d_inst) cudaFree(s->d_inst);
@@ -465,7 +531,12 @@ qg_status qg_set_gaussian(qg_state_t s, int surface, const double* q0, const dou
   if (!s || !q0 || !p0 || !sigma0) return QG_ERR_INVALID_ARG;
   const qg_grid* g = s->m->g;
   if (surface < 0 || surface >= s->m->S) return QG_ERR_INVALID_ARG;
-  if (!(sigma0[0] > 0.0) || !std::isfinite(q0[0]) || !std::isfinite(p0[0])) return QG_ERR_INVALID_ARG;
+  for (int d = 0; d < g->D; ++d)
+    if (!(sigma0[d] > 0.0) || !std::isfinite(q0[d]) || !std::isfinite(p0[d])) return QG_ERR_INVALID_ARG;
+  if (g->D == 2) {
+    QG_TRY(qg_launch_gaussian2d(s->d_psi, g->n, s->m->S, surface, g->qmin, g->dq, q0, p0, sigma0, s->stream));
+    return QG_OK;
+  }
   QG_TRY(qg_launch_gaussian(s->d_psi, g->n[0], s->m->S, surface, g->qmin[0], g->dq[0], q0[0], p0[0], sigma0[0],
                             s->stream));
   return QG_OK;
@@ -475,8 +546,12 @@ qg_status qg_apply_h(qg_state_t s, void* out, int on_device) {
   if (!s || !out) return QG_ERR_INVALID_ARG;
   const qg_grid* g = s->m->g;
   const size_t len = (size_t)s->m->S * g->ntot;
-  double2* dst = on_device ? (double2*)out : s->d_work + 1 * len;  // B slot as staging
-  QG_TRY(qg_launch_apply_h(s->d_inst, dst, g->n[0], s->m->S, s->stream));
+  double2* dst = on_device ? (double2*)out : s->d_work + 2 * len;  // B slot as staging
+  if (g->D == 2) {
+    QG_TRY(qg_launch_apply_h2d(make_inst2d(s), dst, nullptr, s->stream));
+  } else {
+    QG_TRY(qg_launch_apply_h(s->d_inst, dst, g->n[0], s->m->S, s->stream));
+  }
   if (!on_device) {
     QG_TRY(cudaMemcpyAsync(out, dst, sizeof(double2) * len, cudaMemcpyDeviceToHost, s->stream));
     QG_TRY(cudaStreamSynchronize(s->stream));
@@ -508,7 +583,52 @@ static qg_status build_plan(int method, int order, int scheme, double dt, int64_
   P->true_res = o.true_residual;
   P->inner_tol = o.inner_tol;
   P->max_outer = o.max_outer;
+  P->solver = o.solver;
   return QG_OK;
+}
+
+static qg_status check_run(int run, const StepPlan& P, const qg_state* s) {
+  if (run != QG_RUN_FORWARD && run != QG_RUN_CHECKPOINT && run != QG_RUN_ADJOINT) return QG_ERR_INVALID_ARG;
+  if (run == QG_RUN_CHECKPOINT && (!s->adj.ckpt || s->adj.every < 1 || s->adj.nckpt < 1)) return QG_ERR_INVALID_ARG;
+  if (run == QG_RUN_ADJOINT &&
+      (!s->adj.grad || !s->adj.gV || !s->adj.gF || P.restart > QG_MAX_RESTART - 4 || s->adj.every < 1))
+    return QG_ERR_INVALID_ARG;
+  return QG_OK;
+}
+
+qg_status qg_state_set_adjoint(qg_state_t s, void* checkpoints, int64_t ncheckpoints, int64_t every, void* grad,
+                               double* grad_V, double* grad_F) {
+  if (!s || every < 1 || ncheckpoints < 0 || (ncheckpoints > 0 && !checkpoints)) return QG_ERR_INVALID_ARG;
+  s->adj.ckpt = (double2*)checkpoints;
+  s->adj.nckpt = ncheckpoints;
+  s->adj.every = every;
+  s->adj.grad = (double2*)grad;
+  s->adj.gV = grad_V;
+  s->adj.gF = grad_F;
+  return upload_desc(s);
+}
+
+qg_status qg_propagate_ex(qg_state_t s, int run, int method, int order, int scheme, double dt, int64_t nsteps,
+                          const qg_solver_opts* opts, qg_step_stats* stats) {
+  if (!s) return QG_ERR_INVALID_ARG;
+  StepPlan P;
+  qg_status st = build_plan(method, order, scheme, dt, nsteps, opts, &P);
+  if (st != QG_OK) return st;
+  st = check_run(run, P, s);
+  if (st != QG_OK) return st;
+  P.run = run;
+  const qg_grid* g = s->m->g;
+  if (g->D == 2) {
+    if (run == QG_RUN_ADJOINT || P.restart > QG_MAX_RESTART - 1) return QG_ERR_UNSUPPORTED;
+    QG_TRY(qg_launch_propagate2d(make_inst2d(s), P, s->d_stats, s->stream));
+  } else {
+    QG_TRY(qg_launch_propagate(s->d_inst, 1, P, s->d_counter, s->d_stats, g->n[0], s->m->S, s->stream));
+  }
+  qg_step_stats h;
+  QG_TRY(cudaMemcpyAsync(&h, s->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  QG_TRY(cudaStreamSynchronize(s->stream));
+  if (stats) *stats = h;
+  return (qg_status)h.status;
 }
 
 qg_status qg_propagate(qg_state_t s, int method, int order, int scheme, double dt, int64_t nsteps,
@@ -518,7 +638,12 @@ qg_status qg_propagate(qg_state_t s, int method, int order, int scheme, double d
   qg_status st = build_plan(method, order, scheme, dt, nsteps, opts, &P);
   if (st != QG_OK) return st;
   const qg_grid* g = s->m->g;
-  QG_TRY(qg_launch_propagate(s->d_inst, 1, P, s->d_counter, s->d_stats, g->n[0], s->m->S, s->stream));
+  if (g->D == 2) {
+    if (P.restart > QG_MAX_RESTART - 1) return QG_ERR_UNSUPPORTED;
+    QG_TRY(qg_launch_propagate2d(make_inst2d(s), P, s->d_stats, s->stream));
+  } else {
+    QG_TRY(qg_launch_propagate(s->d_inst, 1, P, s->d_counter, s->d_stats, g->n[0], s->m->S, s->stream));
+  }
   qg_step_stats h;
   QG_TRY(cudaMemcpyAsync(&h, s->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
   QG_TRY(cudaStreamSynchronize(s->stream));
@@ -534,25 +659,46 @@ qg_status qg_step_implicit(qg_state_t s, int method, int order, int scheme, doub
 qg_status qg_batch_create(qg_state_t* states, int nstates, qg_batch_t* out) {
   if (!out || !states || nstates < 1) return QG_ERR_INVALID_ARG;
   *out = nullptr;
-  for (int i = 0; i < nstates; ++i)
+  for (int i = 0; i < nstates; ++i) {
     if (!states[i]) return QG_ERR_INVALID_ARG;
+    if (states[i]->m->g->D != 1) return QG_ERR_UNSUPPORTED;
+  }
   qg_batch* b = new (std::nothrow) qg_batch;
   if (!b) return QG_ERR_OOM;
+  memset(b, 0, sizeof(*b));
   b->n = nstates;
   b->stream = states[0]->stream;
-  b->max_n = 0;
-  b->max_S = 0;
-  b->d_desc = nullptr;
-  b->d_stats = nullptr;
-  b->d_counter = nullptr;
-  b->h_stats = nullptr;
-  std::vector<InstDesc> descs(nstates);
-  for (int i = 0; i < nstates; ++i) {
-    descs[i] = make_desc(states[i]);
-    if (descs[i].n > b->max_n) b->max_n = descs[i].n;
-    if (descs[i].S > b->max_S) b->max_S = descs[i].S;
+  b->ctas_per_sm = 1;
+  b->nb_pref = 0;
+  b->order = new (std::nothrow) int[nstates];
+  if (!b->order) {
+    delete b;
+    return QG_ERR_OOM;
   }
-  cudaError_t e = cudaMalloc(&b->d_desc, sizeof(InstDesc) * nstates);
+  std::vector<InstDesc> descs(nstates);
+  std::vector<double> cost(nstates);
+  for (int i = 0; i < nstates; ++i) {
+    const InstDesc d = make_desc(states[i]);
+    if (d.n > b->max_n) b->max_n = d.n;
+    if (d.S > b->max_S) b->max_S = d.S;
+    // work estimate of one H psi: S transforms of n log2 n
+    cost[i] = (double)d.S * d.n * (ilog2h(d.n) + 1);
+    b->order[i] = i;
+  }
+  b->adjoint_ready = true;
+  for (int i = 0; i < nstates; ++i) {
+    const qg_state_adjoint& ad = states[i]->adj;
+    if (!ad.grad || !ad.gV || !ad.gF || !ad.ckpt || ad.nckpt < 1 || ad.every < 1) b->adjoint_ready = false;
+  }
+  // longest estimated work first, so the persistent CTAs finish together
+  std::stable_sort(b->order, b->order + nstates, [&](int x, int y) { return cost[x] > cost[y]; });
+  for (int k = 0; k < nstates; ++k) descs[k] = make_desc(states[b->order[k]]);
+  cudaError_t e = cudaSuccess;
+  if (b->stream == 0) {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamDefault);
+    b->own_stream = (e == cudaSuccess);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, sizeof(InstDesc) * nstates);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_stats, sizeof(qg_step_stats) * nstates);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_stats, sizeof(qg_step_stats) * nstates);
@@ -568,11 +714,27 @@ qg_status qg_batch_create(qg_state_t* states, int nstates, qg_batch_t* out) {
 
 void qg_batch_destroy(qg_batch_t b) {
   if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->d_desc) cudaFree(b->d_desc);
   if (b->d_stats) cudaFree(b->d_stats);
   if (b->d_counter) cudaFree(b->d_counter);
   if (b->h_stats) cudaFreeHost(b->h_stats);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete[] b->order;
   delete b;
+}
+
+static qg_status batch_collect(qg_batch_t b, int32_t* statuses, qg_step_stats* stats) {
+  QG_TRY(cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(qg_step_stats) * b->n, cudaMemcpyDeviceToHost, b->stream));
+  QG_TRY(cudaStreamSynchronize(b->stream));
+  qg_status ret = QG_OK;
+  for (int k = 0; k < b->n; ++k) {
+    const int i = b->order[k];
+    if (statuses) statuses[i] = b->h_stats[k].status;
+    if (stats) stats[i] = b->h_stats[k];
+    if (b->h_stats[k].status != QG_OK) ret = QG_ERR_NOT_CONVERGED;
+  }
+  return ret;
 }
 
 qg_status qg_batch_run(qg_batch_t b, int method, int order, int scheme, double dt, int64_t nsteps,
@@ -581,17 +743,149 @@ qg_status qg_batch_run(qg_batch_t b, int method, int order, int scheme, double d
   StepPlan P;
   qg_status st = build_plan(method, order, scheme, dt, nsteps, opts, &P);
   if (st != QG_OK) return st;
-  QG_TRY(qg_launch_propagate(b->d_desc, b->n, P, b->d_counter, b->d_stats, b->max_n, b->max_S, b->stream));
-  QG_TRY(cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(qg_step_stats) * b->n, cudaMemcpyDeviceToHost, b->stream));
-  QG_TRY(cudaStreamSynchronize(b->stream));
-  qg_status ret = QG_OK;
-  for (int i = 0; i < b->n; ++i) {
-    if (statuses) statuses[i] = b->h_stats[i].status;
-    if (stats) stats[i] = b->h_stats[i];
-    if (b->h_stats[i].status != QG_OK) ret = QG_ERR_NOT_CONVERGED;
-  }
-  return ret;
+  QG_TRY(qg_launch_propagate_tuned(b->d_desc, b->n, P, b->d_counter, b->d_stats, b->max_n, b->max_S, b->ctas_per_sm,
+                                   b->nb_pref, b->stream));
+  return batch_collect(b, statuses, stats);
 }
+
+qg_status qg_batch_run_ex(qg_batch_t b, int run, int method, int order, int scheme, double dt, int64_t nsteps,
+                          const qg_solver_opts* opts, int32_t* statuses, qg_step_stats* stats) {
+  if (!b) return QG_ERR_INVALID_ARG;
+  StepPlan P;
+  qg_status st = build_plan(method, order, scheme, dt, nsteps, opts, &P);
+  if (st != QG_OK) return st;
+  if (run != QG_RUN_FORWARD && run != QG_RUN_CHECKPOINT && run != QG_RUN_ADJOINT) return QG_ERR_INVALID_ARG;
+  if (run == QG_RUN_ADJOINT && P.restart > QG_MAX_RESTART - 4) return QG_ERR_INVALID_ARG;
+  if (run != QG_RUN_FORWARD && !b->adjoint_ready) return QG_ERR_INVALID_ARG;
+  P.run = run;
+  QG_TRY(qg_launch_propagate_tuned(b->d_desc, b->n, P, b->d_counter, b->d_stats, b->max_n, b->max_S, b->ctas_per_sm,
+                                   b->nb_pref, b->stream));
+  return batch_collect(b, statuses, stats);
+}
+
+qg_status qg_batch_capture(qg_batch_t b, int method, int order, int scheme, double dt, int64_t nsteps,
+                           const qg_solver_opts* opts) {
+  if (!b) return QG_ERR_INVALID_ARG;
+  StepPlan P;
+  qg_status st = build_plan(method, order, scheme, dt, nsteps, opts, &P);
+  if (st != QG_OK) return st;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  // function attributes are set here, outside the capture, by a zero-instance
+  // launch that the kernel leaves immediately
+  QG_TRY(qg_launch_propagate_tuned(b->d_desc, 0, P, b->d_counter, b->d_stats, b->max_n, b->max_S, b->ctas_per_sm,
+                                   b->nb_pref, b->stream));
+  QG_TRY(cudaStreamSynchronize(b->stream));
+  cudaGraph_t g = nullptr;
+  QG_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = qg_launch_propagate_tuned(b->d_desc, b->n, P, b->d_counter, b->d_stats, b->max_n, b->max_S,
+                                            b->ctas_per_sm, b->nb_pref, b->stream);
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_err("qg_batch_capture", e);
+    b->graph = nullptr;
+    return QG_ERR_CUDA;
+  }
+  return QG_OK;
+}
+
+qg_status qg_batch_autotune(qg_batch_t b, int method, int order, int scheme, double dt, int64_t trial_steps,
+                            const qg_solver_opts* opts, double* ms_out /* 4 entries or NULL */) {
+  if (!b || trial_steps < 1) return QG_ERR_INVALID_ARG;
+  StepPlan P;
+  qg_status st = build_plan(method, order, scheme, dt, trial_steps, opts, &P);
+  if (st != QG_OK) return st;
+  // save every state, time each candidate launch shape on the real batch,
+  // restore the states after each trial
+  std::vector<InstDesc> descs(b->n);
+  QG_TRY(cudaMemcpy(descs.data(), b->d_desc, sizeof(InstDesc) * b->n, cudaMemcpyDeviceToHost));
+  size_t total = 0;
+  for (const InstDesc& d : descs) total += (size_t)d.S * d.n;
+  double2* save = nullptr;
+  QG_TRY(cudaMalloc(&save, sizeof(double2) * total));
+  auto copy_all = [&](bool to_save) -> cudaError_t {
+    size_t off = 0;
+    for (const InstDesc& d : descs) {
+      const size_t len = (size_t)d.S * d.n;
+      cudaError_t e = to_save ? cudaMemcpyAsync(save + off, d.psi, sizeof(double2) * len, cudaMemcpyDeviceToDevice,
+                                                b->stream)
+                              : cudaMemcpyAsync(d.psi, save + off, sizeof(double2) * len, cudaMemcpyDeviceToDevice,
+                                                b->stream);
+      if (e != cudaSuccess) return e;
+      off += len;
+    }
+    return cudaSuccess;
+  };
+  const int cand[4][2] = {{1, 0}, {1, 1}, {2, 0}, {2, 1}};
+  double best = 1e300;
+  int bi = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = copy_all(true);
+  for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+    float ms = -1.f;
+    e = cudaEventRecord(e0, b->stream);
+    cudaError_t el = qg_launch_propagate_tuned(b->d_desc, b->n, P, b->d_counter, b->d_stats, b->max_n, b->max_S,
+                                               cand[c][0], cand[c][1], b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (el == cudaSuccess && e == cudaSuccess) {
+      cudaEventElapsedTime(&ms, e0, e1);
+    } else if (el == cudaErrorInvalidConfiguration) {
+      cudaGetLastError();   // shape does not fit: skip it
+      ms = -1.f;
+    } else if (e == cudaSuccess) {
+      e = el;
+    }
+    if (ms_out) ms_out[c] = ms;
+    if (ms > 0.f && ms < best) {
+      best = ms;
+      bi = c;
+    }
+    if (e == cudaSuccess) e = copy_all(false);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(save);
+  if (e != cudaSuccess) {
+    set_err("qg_batch_autotune", e);
+    return QG_ERR_CUDA;
+  }
+  b->ctas_per_sm = cand[bi][0];
+  b->nb_pref = cand[bi][1];
+  if (b->graph) {   // a captured graph used the old launch shape
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return QG_OK;
+}
+
+qg_status qg_batch_tuning(qg_batch_t b, int* ctas_per_sm, int* surfaces_per_fft) {
+  if (!b) return QG_ERR_INVALID_ARG;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  if (surfaces_per_fft) *surfaces_per_fft = b->nb_pref;
+  return QG_OK;
+}
+
+qg_status qg_batch_replay(qg_batch_t b) {
+  if (!b || !b->graph) return QG_ERR_INVALID_ARG;
+  QG_TRY(cudaGraphLaunch(b->graph, b->stream));
+  return QG_OK;
+}
+
+qg_status qg_batch_stats(qg_batch_t b, int32_t* statuses, qg_step_stats* stats) {
+  if (!b) return QG_ERR_INVALID_ARG;
+  return batch_collect(b, statuses, stats);
+}
+
+void* qg_batch_stream(qg_batch_t b) { return b ? (void*)b->stream : nullptr; }
 
 qg_status qg_batch_propagate(qg_state_t* states, int nstates, int method, int order, int scheme, double dt,
                              int64_t nsteps, const qg_solver_opts* opts, int32_t* statuses, qg_step_stats* stats) {
@@ -617,7 +911,7 @@ qg_status qg_norm(qg_state_t s, double* out) {
 qg_status qg_population(qg_state_t s, double* out) {
   if (!s || !out) return QG_ERR_INVALID_ARG;
   const qg_grid* g = s->m->g;
-  QG_TRY(qg_launch_populations(s->d_psi, g->n[0], s->m->S, g->dq[0], s->d_scalars, s->stream));
+  QG_TRY(qg_launch_populations(s->d_psi, g->ntot, s->m->S, grid_dv(g), s->d_scalars, s->stream));
   QG_TRY(cudaMemcpyAsync(out, s->d_scalars, sizeof(double) * s->m->S, cudaMemcpyDeviceToHost, s->stream));
   QG_TRY(cudaStreamSynchronize(s->stream));
   return QG_OK;
@@ -626,7 +920,12 @@ qg_status qg_population(qg_state_t s, double* out) {
 qg_status qg_energy(qg_state_t s, double* out) {
   if (!s || !out) return QG_ERR_INVALID_ARG;
   const qg_grid* g = s->m->g;
-  QG_TRY(qg_launch_energy(s->d_inst, s->d_scalars, g->n[0], s->m->S, s->stream));
+  if (g->D == 2) {
+    QG_TRY(qg_launch_apply_h2d(make_inst2d(s), s->d_work + (size_t)2 * s->m->S * g->ntot, s->d_scalars,
+                               s->stream));
+  } else {
+    QG_TRY(qg_launch_energy(s->d_inst, s->d_scalars, g->n[0], s->m->S, s->stream));
+  }
   double v[2];
   QG_TRY(cudaMemcpyAsync(v, s->d_scalars, sizeof(v), cudaMemcpyDeviceToHost, s->stream));
   QG_TRY(cudaStreamSynchronize(s->stream));
@@ -639,7 +938,7 @@ qg_status qg_overlap(qg_state_t a, qg_state_t b, double* out) {
   if (a->m->S != b->m->S || a->m->g->ntot != b->m->g->ntot) return QG_ERR_INVALID_ARG;
   const size_t len = (size_t)a->m->S * a->m->g->ntot;
   QG_TRY(cudaStreamSynchronize(b->stream));
-  QG_TRY(qg_launch_overlap(a->d_psi, b->d_psi, (int)len, a->m->g->dq[0], a->d_scalars, a->stream));
+  QG_TRY(qg_launch_overlap(a->d_psi, b->d_psi, (int)len, grid_dv(a->m->g), a->d_scalars, a->stream));
   QG_TRY(cudaMemcpyAsync(out, a->d_scalars, sizeof(double) * 2, cudaMemcpyDeviceToHost, a->stream));
   QG_TRY(cudaStreamSynchronize(a->stream));
   return QG_OK;
@@ -723,6 +1022,7 @@ qg_status qg_propagate_noalloc(int N, double qmin, double qmax, int S, double ma
   P.true_res = o.true_residual;
   P.inner_tol = o.inner_tol;
   P.max_outer = o.max_outer;
+  P.solver = o.solver;
   const FftPlan plan = make_plan(N);
   qg_step_stats h;
   memset(&h, 0, sizeof(h));

@@ -347,4 +347,28 @@ __device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T
   }
 }
 
+// y = (D + F) x (one half of H psi; used by the adjoint to form the field
+// gradients).  y must not alias x.
+template <typename R>
+__device__ __forceinline__ void apply_d_plus_f(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
+                                               const typename Cx<R>::T* x, typename Cx<R>::T* y) {
+  using C = typename Cx<R>::T;
+  const int n = H.n, S = H.S;
+  const int ln = ilog2(n);
+  const int nb = (S <= nb_cap) ? S : 1;
+  for (int s0 = 0; s0 < S; s0 += nb) {
+    for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[i] = x[s0 * n + i];
+    __syncthreads();
+    spectral_derivative<R>(sbuf, nb, H);
+    for (int i = threadIdx.x; i < nb * n; i += kThreads) {
+      const int s = s0 + (i >> ln), j = i & (n - 1);
+      C acc = sbuf[i];
+      for (int t = 0; t < S; ++t)
+        if (t != s) acc = caxpy_r(coupling(H, s, t, j), x[t * n + j], acc);
+      y[s * n + j] = acc;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace qg

@@ -7,7 +7,8 @@
 #include "qgeom.h"
 
 #define QG_MAX_S 4
-#define QG_MAX_D 1
+#define QG_MAX_D 2
+#define QG_MAX_2D_POINTS (1 << 20)
 #define QG_MAX_RESTART 64
 #define QG_MAX_PASSES 8
 #define QG_MAX_FRACTIONS 128
@@ -53,6 +54,15 @@ struct qg_model {
 
 struct InstDesc;
 
+struct qg_state_adjoint {
+  double2* ckpt;
+  long long nckpt;
+  long long every;
+  double2* grad;
+  double* gV;
+  double* gF;
+};
+
 struct qg_state {
   qg_model* m;
   InstDesc* d_inst;         // this state's instance descriptor (device)
@@ -65,6 +75,8 @@ struct qg_state {
   cudaStream_t stream;
   qg_step_stats* d_stats;   // one record
   double* d_scalars;        // small device scratch for observables
+  qg_state_adjoint adj;     // caller-owned adjoint buffers (or nulls)
+  unsigned char* d_coop;    // 2-D grids: barrier words, error flag, partial sums
 };
 
 // Everything one CTA needs to work on one instance (a state with its model
@@ -89,6 +101,41 @@ struct InstDesc {
   const float* V32;
   const float* F32;
   float2* work32;  // mixed: U32, r32, d32, then inner basis (each S * n)
+  // adjoint buffers (caller-owned device memory, optional)
+  double2* ckpt;       // checkpoints: nckpt vectors of S * n
+  long long nckpt;
+  long long every;     // composed steps between checkpoints
+  double2* grad;       // in: dL/dpsi(t_f); out: dL/dpsi(0)   (S * n)
+  double* gV;          // += dL/dV   (S * n)
+  double* gF;          // += dL/dF   (S(S-1)/2 * n)
+};
+
+// One instance on a 2-D grid (all CTAs of a cooperative launch share it).
+struct Inst2D {
+  int n[2];
+  int S;
+  int npass[2];
+  int radix[2][QG_MAX_PASSES];
+  double h2m[2];
+  double dv;
+  const double2* tw[2];
+  const double* kd[2];
+  const float2* tw32[2];
+  const float* kd32[2];
+  const double* V;     // S * N
+  const double* F;     // 2 * S(S-1)/2 * N
+  const float* V32;
+  const float* F32;
+  double2* psi;
+  double2* work;       // U, T, B, X, P0, basis (m + 1)
+  float2* work32;      // U, T, r, d, basis (m + 1)
+  int precision;
+  unsigned* bar;       // grid barrier: count, generation
+  int* err;            // barrier time-out flag
+  double* gred;        // 2 x gridDim x 32 partial sums
+  double2* ckpt;
+  long long nckpt;
+  long long every;
 };
 
 // Parameters of one propagate launch (passed by value).
@@ -105,23 +152,34 @@ struct StepPlan {
   int true_res;
   double inner_tol;
   int max_outer;
+  int run;   // QG_RUN_FORWARD, QG_RUN_CHECKPOINT or QG_RUN_ADJOINT
+  int solver;  // QG_SOLVER_GMRES or QG_SOLVER_LANCZOS
   double frac[QG_MAX_FRACTIONS];
 };
 
 struct qg_batch {
   int n;
   int max_n, max_S;
-  cudaStream_t stream;
-  InstDesc* d_desc;
-  qg_step_stats* d_stats;
+  cudaStream_t stream;      // the states' stream, or a private stream when that is the legacy stream
+  bool own_stream;
+  InstDesc* d_desc;         // instance table, longest estimated work first
+  int* order;               // order[k] = index (into the caller's list) of table entry k
+  qg_step_stats* d_stats;   // per table entry
   int* d_counter;
-  qg_step_stats* h_stats;   // pinned
+  qg_step_stats* h_stats;   // pinned, per table entry
+  cudaGraphExec_t graph;    // captured run, or null
+  bool adjoint_ready;       // every state has checkpoint and gradient buffers
+  int ctas_per_sm;          // launch shape chosen by qg_batch_autotune (default 1)
+  int nb_pref;              // surfaces per FFT batch (0 = as many as fit)
 };
 
 // Launch wrappers (qg_kernels.cu).
 size_t qg_smem_bytes(int max_n, int max_S, int restart);
 cudaError_t qg_launch_propagate(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
                                 qg_step_stats* d_stats, int max_n, int max_S, cudaStream_t st);
+cudaError_t qg_launch_propagate_tuned(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
+                                      qg_step_stats* d_stats, int max_n, int max_S, int ctas_per_sm, int nb_pref,
+                                      cudaStream_t st);
 cudaError_t qg_launch_apply_h(const InstDesc* d_inst, double2* d_out, int n, int S, cudaStream_t st);
 cudaError_t qg_launch_energy(const InstDesc* d_inst, double* d_out, int n, int S, cudaStream_t st);
 cudaError_t qg_launch_populations(const double2* d_psi, int n, int S, double dq, double* d_out, cudaStream_t st);
@@ -132,6 +190,13 @@ cudaError_t qg_launch_gaussian(double2* d_psi, int n, int S, int surface, double
 cudaError_t qg_noalloc_launch(int n, double qmin, double qmax, int S, double mass, const double* V, const double* F,
                               double2* psi, const FftPlan& plan, const StepPlan& P, qg_step_stats* host_stats,
                               cudaStream_t st);
+cudaError_t qg_launch_propagate2d(const Inst2D& I, const StepPlan& P, qg_step_stats* d_stats, cudaStream_t st);
+cudaError_t qg_launch_apply_h2d(const Inst2D& I, double2* d_out, double* d_energy, cudaStream_t st);
+cudaError_t qg_launch_gaussian2d(double2* d_psi, const int* n, int S, int surface, const double* qmin,
+                                 const double* dq, const double* q0, const double* p0, const double* s0,
+                                 cudaStream_t st);
 cudaError_t qg_launch_to_f32(const double* d_in, float* d_out, size_t n, cudaStream_t st);
-cudaError_t qg_launch_fields2(const double* d_W, const double* d_dW, int n, double* d_V, double* d_F,
+cudaError_t qg_launch_fieldsS(const double* d_W, const double* d_dW, int n, int S, double* d_V, double* d_F,
+                              double* d_vec, cudaStream_t st);
+cudaError_t qg_launch_fields2(const double* d_W, const double* d_dW, int n, int D, double* d_V, double* d_F,
                               cudaStream_t st);

@@ -5,26 +5,13 @@
 // adiabatic field builder.
 #include <cuda_runtime.h>
 
-#include "qg_device.cuh"
+#include "qg_solver.cuh"
 
 namespace qg {
 
-__device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
-
-// Small GMRES arrays of one precision in shared memory.
-template <typename R>
-struct GSmem {
-  using C = typename Cx<R>::T;
-  C* hess;   // (m + 1) * m, column j at hess + j * (m + 1)
-  C* g;      // m + 1
-  C* gs;     // m   Givens s
-  R* gc;     // m   Givens c
-  C* y;      // m
-};
-
-// Dynamic shared memory: the FFT buffer (nb_cap vectors of max_n complex
-// doubles, also used by the FP32 passes), then the GMRES arrays sized for
-// doubles (the FP32 arrays fit in the same space).
+// Dynamic shared memory of the 1-D kernels: the FFT buffer (nb_cap vectors of
+// max_n complex doubles, also used by the FP32 passes), then the GMRES arrays
+// sized for doubles (the FP32 arrays fit in the same space).
 struct Smem {
   unsigned char* fft;
   unsigned char* gm;
@@ -41,36 +28,6 @@ __device__ Smem carve_smem(void* base, int max_n, int nb_cap, int m) {
   s.m = m;
   return s;
 }
-
-template <typename R>
-__device__ GSmem<R> gsmem(const Smem& s) {
-  using C = typename Cx<R>::T;
-  GSmem<R> g;
-  const int m = s.m;
-  unsigned char* p = s.gm;
-  g.hess = reinterpret_cast<C*>(p);
-  p += align16(sizeof(double2) * (size_t)(m + 1) * m);
-  g.g = reinterpret_cast<C*>(p);
-  p += align16(sizeof(double2) * (size_t)(m + 1));
-  g.gs = reinterpret_cast<C*>(p);
-  p += align16(sizeof(double2) * (size_t)m);
-  g.y = reinterpret_cast<C*>(p);
-  p += align16(sizeof(double2) * (size_t)m);
-  g.gc = reinterpret_cast<R*>(p);
-  return g;
-}
-
-struct Counters {
-  long long hpsi;
-  long long hpsi32;
-  long long krylov;
-  long long ortho;
-  long long update;
-  long long restart;
-  long long outer;
-  int max_krylov;
-  double max_res;
-};
 
 // H psi operands of an instance in one precision; scratch vector U given.
 __device__ __forceinline__ HOp<double> hop64(const InstDesc& I, double2* U) {
@@ -103,374 +60,180 @@ __device__ __forceinline__ HOp<float> hop32(const InstDesc& I, float2* U) {
   return H;
 }
 
-struct SolveParams {
-  double tol;
-  int m;
-  int max_iters;
-  int reorth;
-  int true_res;
+// One CTA owns one whole 1-D instance.
+struct Dom1D {
+  int len;
+  double dv;
+  unsigned char* gm;
+  double* red;
+  HOp<double> H64;
+  HOp<float> H32;
+  unsigned char* fb;
+  int nb_cap;
+  double2* basis64;
+  double2* res64;
+  float2* r32;
+  float2* d32;
+  float2* basis32;
+
+  template <class F>
+  __device__ __forceinline__ void each(F&& f) {
+    for (int i = threadIdx.x; i < len; i += kThreads) f(i);
+  }
+  template <int K, typename R>
+  __device__ __forceinline__ bool sum(R (&v)[K], R* out) {
+    cta_sum<K>(v, reinterpret_cast<R*>(red), out);
+    return true;
+  }
+  template <typename R>
+  __device__ __forceinline__ void hpsi(const typename Cx<R>::T* x, typename Cx<R>::T* y,
+                                       const typename Cx<R>::T* z, R e, R a, typename Cx<R>::T c) {
+    if constexpr (sizeof(R) == 8)
+      apply_h_axpby<double>(H64, reinterpret_cast<double2*>(fb), nb_cap, x, y, z, e, a, c);
+    else
+      apply_h_axpby<float>(H32, reinterpret_cast<float2*>(fb), 2 * nb_cap, x, y, z, e, a, c);
+  }
+  __device__ __forceinline__ bool ok() const { return true; }
 };
 
-// Solve (1 + i tau H) x = b by restarted GMRES (Sec. II B) in the grid inner
-// product, in precision R.  X holds the initial guess on entry and the
-// solution on exit; basis holds m + 1 vectors.  Returns true on convergence
-// (estimated relative residual <= tol).  *res_out receives the final
-// relative residual estimate.
-template <typename R>
-__device__ bool gmres_solve(const HOp<R>& H, const Smem& smem, const SolveParams& P, R dv, R tau,
-                            const typename Cx<R>::T* b, typename Cx<R>::T* X, typename Cx<R>::T* basis,
-                            Counters& cnt, R* red, R* sc, double* res_out) {
-  using C = typename Cx<R>::T;
-  const GSmem<R> sm = gsmem<R>(smem);
-  C* fbuf = reinterpret_cast<C*>(smem.fft);
-  const int nbc = sizeof(R) == 8 ? smem.nb_cap : 2 * smem.nb_cap;
-  const int len = H.S * H.n;
-  const int m = P.m;
-  const C ic = cmk<C>((R)0, tau);     // A = 1 + i tau H
-  const C mic = cmk<C>((R)0, -tau);
-  const R bn = sqrt(dv * cta_norm2(b, len, red, sc));
-  const R target = (R)P.tol * bn;
-  int total = 0;
-  // r0 = b - A X
-  apply_h_axpby<R>(H, fbuf, nbc, X, basis, b, (R)1, (R)-1, mic);
-  if (sizeof(R) == 8) cnt.hpsi++; else cnt.hpsi32++;
-  for (int guard = 0; guard < P.max_iters + 2; ++guard) {
-    C* V0 = basis;
-    const R beta = sqrt(dv * cta_norm2(V0, len, red, sc));
-    if (beta <= target || bn == (R)0) {
-      *res_out = (bn > (R)0) ? (double)(beta / bn) : 0.0;
-      if (total > cnt.max_krylov) cnt.max_krylov = total;
-      return true;
-    }
-    if (total >= P.max_iters) break;
-    const R ib = (R)1 / beta;
-    for (int i = threadIdx.x; i < len; i += kThreads) V0[i] = cscale(ib, V0[i]);
-    if (threadIdx.x == 0) {
-      sm.g[0] = cmk<C>(beta, (R)0);
-      for (int i = 1; i <= m; ++i) sm.g[i] = cmk<C>((R)0, (R)0);
-    }
-    __syncthreads();
-    int ncol = 0;
-    bool conv = false;
-    R res_est = beta;
-    for (int j = 0; j < m; ++j) {
-      C* Vj = basis + (size_t)j * len;
-      C* W = basis + (size_t)(j + 1) * len;
-      apply_h_axpby<R>(H, fbuf, nbc, Vj, W, nullptr, (R)0, (R)1, ic);
-      if (sizeof(R) == 8) cnt.hpsi++; else cnt.hpsi32++;
-      C* hcol = sm.hess + (size_t)j * (m + 1);
-      if (threadIdx.x <= j + 1) hcol[threadIdx.x] = cmk<C>((R)0, (R)0);
-      __syncthreads();
-      // Classical Gram-Schmidt, optionally repeated once (CGS2).
-      for (int pass = 0; pass < (P.reorth ? 2 : 1); ++pass) {
-        for (int c0 = 0; c0 <= j; c0 += 8) {
-          const int nc = min(8, j + 1 - c0);
-          R v[16];
-#pragma unroll
-          for (int k = 0; k < 16; ++k) v[k] = (R)0;
-          for (int i = threadIdx.x; i < len; i += kThreads) {
-            const C w = W[i];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              if (k < nc) {
-                const C q = basis[(size_t)(c0 + k) * len + i];
-                v[2 * k] = fma(q.x, w.x, fma(q.y, w.y, v[2 * k]));
-                v[2 * k + 1] = fma(q.x, w.y, fma(-q.y, w.x, v[2 * k + 1]));
-              }
-            }
-          }
-          cta_sum<16>(v, red, sc);
-          if (threadIdx.x < nc) {
-            const C h = cmk<C>(dv * sc[2 * threadIdx.x], dv * sc[2 * threadIdx.x + 1]);
-            hcol[c0 + threadIdx.x] = cadd(hcol[c0 + threadIdx.x], h);
-            sc[32 + 2 * threadIdx.x] = h.x;
-            sc[33 + 2 * threadIdx.x] = h.y;
-          }
-          __syncthreads();
-          C hk[8];
-#pragma unroll
-          for (int k = 0; k < 8; ++k)
-            hk[k] = (k < nc) ? cmk<C>(sc[32 + 2 * k], sc[33 + 2 * k]) : cmk<C>((R)0, (R)0);
-          __syncthreads();
-          for (int i = threadIdx.x; i < len; i += kThreads) {
-            C w = W[i];
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-              if (k < nc) w = cnaxpy(hk[k], basis[(size_t)(c0 + k) * len + i], w);
-            W[i] = w;
-          }
-          __syncthreads();
-        }
-      }
-      const R hn = sqrt(dv * cta_norm2(W, len, red, sc));
-      const R tiny = sizeof(R) == 8 ? (R)1e-300 : (R)1e-35;
-      if (hn > tiny) {
-        const R ih = (R)1 / hn;
-        for (int i = threadIdx.x; i < len; i += kThreads) W[i] = cscale(ih, W[i]);
-      }
-      if (threadIdx.x == 0) {
-        hcol[j + 1] = cmk<C>(hn, (R)0);
-        // previous rotations
-        for (int i = 0; i < j; ++i) {
-          const R c = sm.gc[i];
-          const C s = sm.gs[i];
-          const C h0 = hcol[i], h1 = hcol[i + 1];
-          const C t = caxpy(s, h1, cscale(c, h0));                    // c h0 + s h1
-          const C u = cnaxpy(cmk<C>(s.x, -s.y), h0, cscale(c, h1));   // -conj(s) h0 + c h1
-          hcol[i] = t;
-          hcol[i + 1] = u;
-        }
-        // new rotation zeroing hcol[j+1]
-        const C a = hcol[j];
-        const R bb = hcol[j + 1].x;
-        const R aa = hypot(a.x, a.y);
-        R c;
-        C s, r;
-        if (bb == (R)0) {
-          c = (R)1;
-          s = cmk<C>((R)0, (R)0);
-          r = a;
-        } else if (aa == (R)0) {
-          c = (R)0;
-          s = cmk<C>((R)1, (R)0);
-          r = cmk<C>(bb, (R)0);
-        } else {
-          const R rho = hypot(aa, bb);
-          const C ph = cmk<C>(a.x / aa, a.y / aa);
-          c = aa / rho;
-          s = cmk<C>(ph.x * bb / rho, ph.y * bb / rho);
-          r = cmk<C>(ph.x * rho, ph.y * rho);
-        }
-        sm.gc[j] = c;
-        sm.gs[j] = s;
-        hcol[j] = r;
-        hcol[j + 1] = cmk<C>((R)0, (R)0);
-        const C gj = sm.g[j];
-        sm.g[j + 1] = cmk<C>(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
-        sm.g[j] = cscale(c, gj);
-        sc[0] = hypot(sm.g[j + 1].x, sm.g[j + 1].y);
-      }
-      __syncthreads();
-      res_est = sc[0];
-      __syncthreads();
-      ncol = j + 1;
-      cnt.ortho += j + 1;
-      total++;
-      cnt.krylov++;
-      if (res_est <= target) {
-        conv = true;
-        break;
-      }
-      if (total >= P.max_iters || hn <= tiny) break;
-    }
-    // y = R^{-1} g (upper triangular ncol x ncol)
-    if (threadIdx.x == 0) {
-      for (int i = ncol - 1; i >= 0; --i) {
-        C acc = sm.g[i];
-        for (int k = i + 1; k < ncol; ++k) acc = cnaxpy(sm.hess[(size_t)k * (m + 1) + i], sm.y[k], acc);
-        const C d = sm.hess[(size_t)i * (m + 1) + i];
-        const R dd = (R)1 / fma(d.x, d.x, d.y * d.y);
-        sm.y[i] = cmk<C>((acc.x * d.x + acc.y * d.y) * dd, (acc.y * d.x - acc.x * d.y) * dd);
-      }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < len; i += kThreads) {
-      C x = X[i];
-      for (int k = 0; k < ncol; ++k) x = caxpy(sm.y[k], basis[(size_t)k * len + i], x);
-      X[i] = x;
-    }
-    cnt.update += ncol;
-    __syncthreads();
-    if (conv && !P.true_res) {
-      *res_out = (bn > (R)0) ? (double)(res_est / bn) : 0.0;
-      if (total > cnt.max_krylov) cnt.max_krylov = total;
-      return true;
-    }
-    if (total >= P.max_iters && !conv) break;
-    // restart (or true-residual check): V0 = b - A X
-    apply_h_axpby<R>(H, fbuf, nbc, X, basis, b, (R)1, (R)-1, mic);
-    if (sizeof(R) == 8) cnt.hpsi++; else cnt.hpsi32++;
-    cnt.restart++;
-  }
-  if (total > cnt.max_krylov) cnt.max_krylov = total;
-  *res_out = 1e300;
-  return false;
-}
-
-template <typename C>
-__device__ __forceinline__ void vcopy(C* dst, const C* src, int len) {
-  for (int i = threadIdx.x; i < len; i += kThreads) dst[i] = src[i];
-  __syncthreads();
-}
-
-// FP64 implicit solve (1 + i tau H) X = b with GMRES in FP64.
-__device__ bool solve_fp64(const InstDesc& I, const Smem& sm, const StepPlan& P, double tau, const double2* b,
-                           double2* X, Counters& cnt, double* red, double* sc) {
+__device__ Dom1D make_dom1d(const InstDesc& I, const Smem& sm, int m, double* red) {
   const int len = I.S * I.n;
-  const HOp<double> H = hop64(I, I.work);
-  SolveParams sp{P.tol, P.restart, P.max_iters, P.reorth, P.true_res};
-  double res = 0.0;
-  const bool ok = gmres_solve<double>(H, sm, sp, I.dq, tau, b, X, I.work + (size_t)4 * len, cnt, red, sc, &res);
-  if (ok && res > cnt.max_res) cnt.max_res = res;
-  if (!ok) cnt.max_res = 1e300;
-  return ok;
-}
-
-// Mixed-precision implicit solve: FP64 residual r = b - (1 + i tau H) X,
-// complex64 GMRES for (1 + i tau H) d = r / ||r|| to inner_tol, X += ||r|| d,
-// until ||r|| <= tol ||b||.
-__device__ bool solve_mixed(const InstDesc& I, const Smem& sm, const StepPlan& P, double tau, const double2* b,
-                            double2* X, Counters& cnt, double* red, double* sc) {
-  const int len = I.S * I.n;
-  const HOp<double> H64 = hop64(I, I.work);
-  double2* Rv = I.work + (size_t)4 * len;          // FP64 residual
-  const HOp<float> H32 = hop32(I, I.work32);
-  float2* r32 = I.work32 + (size_t)1 * len;
-  float2* d32 = I.work32 + (size_t)2 * len;
-  float2* basis32 = I.work32 + (size_t)3 * len;
-  float* redf = reinterpret_cast<float*>(red);
-  float* scf = reinterpret_cast<float*>(sc);
-  const double2 mic = make_double2(0.0, -tau);
-  const double dv = I.dq;
-  const double bn = sqrt(dv * cta_norm2(b, len, red, sc));
-  const double target = P.tol * bn;
-  SolveParams sp{P.inner_tol, P.restart, P.max_iters, P.reorth, 0};
-  for (int outer = 0; outer <= P.max_outer; ++outer) {
-    apply_h_axpby<double>(H64, reinterpret_cast<double2*>(sm.fft), sm.nb_cap, X, Rv, b, 1.0, -1.0, mic);
-    cnt.hpsi++;
-    const double rho = sqrt(dv * cta_norm2(Rv, len, red, sc));
-    if (rho <= target || bn == 0.0) {
-      const double r = bn > 0.0 ? rho / bn : 0.0;
-      if (r > cnt.max_res) cnt.max_res = r;
-      return true;
-    }
-    if (outer == P.max_outer) break;
-    cnt.outer++;
-    const double ir = 1.0 / rho;
-    for (int i = threadIdx.x; i < len; i += kThreads) {
-      const double2 v = Rv[i];
-      r32[i] = make_float2((float)(v.x * ir), (float)(v.y * ir));
-      d32[i] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    double res = 0.0;
-    gmres_solve<float>(H32, sm, sp, (float)dv, (float)tau, r32, d32, basis32, cnt, redf, scf, &res);
-    for (int i = threadIdx.x; i < len; i += kThreads) {
-      const float2 d = d32[i];
-      const double2 x = X[i];
-      X[i] = make_double2(fma(rho, (double)d.x, x.x), fma(rho, (double)d.y, x.y));
-    }
-    __syncthreads();
+  Dom1D D;
+  D.len = len;
+  D.dv = I.dq;
+  D.gm = sm.gm;
+  D.red = red;
+  D.H64 = hop64(I, I.work);
+  D.fb = sm.fft;
+  D.nb_cap = sm.nb_cap;
+  D.basis64 = I.work + (size_t)4 * len;
+  D.res64 = I.work + (size_t)4 * len;     // mixed form: the FP64 basis is unused
+  if (I.work32) {
+    D.H32 = hop32(I, I.work32);
+    D.r32 = I.work32 + (size_t)1 * len;
+    D.d32 = I.work32 + (size_t)2 * len;
+    D.basis32 = I.work32 + (size_t)3 * len;
+  } else {
+    D.r32 = D.d32 = D.basis32 = nullptr;
   }
-  cnt.max_res = 1e300;
-  return false;
-}
-
-// Explicit-Euler initial guess X = (1 - i tau H) src, in complex64 for the
-// mixed-precision form (only the starting point of the refinement).
-__device__ void guess_mixed(const InstDesc& I, const Smem& sm, double tau, const double2* src, double2* X,
-                            Counters& cnt) {
-  const int len = I.S * I.n;
-  const HOp<float> H32 = hop32(I, I.work32);
-  float2* s32 = I.work32 + (size_t)1 * len;
-  float2* y32 = I.work32 + (size_t)2 * len;
-  for (int i = threadIdx.x; i < len; i += kThreads) {
-    const double2 v = src[i];
-    s32[i] = make_float2((float)v.x, (float)v.y);
-  }
-  __syncthreads();
-  apply_h_axpby<float>(H32, reinterpret_cast<float2*>(sm.fft), 2 * sm.nb_cap, s32, y32, nullptr, 0.f, 1.f,
-                       make_float2(0.f, (float)-tau));
-  cnt.hpsi32++;
-  for (int i = threadIdx.x; i < len; i += kThreads) {
-    const float2 y = y32[i];
-    X[i] = make_double2((double)y.x, (double)y.y);
-  }
-  __syncthreads();
+  return D;
 }
 
 // All nsteps composed steps of one instance.
 __device__ void run_instance(const InstDesc& I, const StepPlan& P, const Smem& sm, qg_step_stats* st, double* red,
                              double* sc) {
   const int len = I.S * I.n;
-  const bool mixed = I.precision == QG_C64_MIXED;
+  Dom1D D = make_dom1d(I, sm, P.restart, red);
+  Counters cnt{0, 0, 0, 0, 0, 0, 0, 0, 0.0};
+  long long nsub = 0;
+  const long long failed =
+      run_steps(D, P, I.psi, I.work + (size_t)1 * len, I.work + (size_t)2 * len, I.work + (size_t)3 * len,
+                I.precision == QG_C64_MIXED, I.ckpt, I.nckpt, I.every, cnt, nsub, sc);
+  write_stats(st, cnt, nsub, failed);
+}
+
+// Adjoint of nsteps composed steps (reverse-mode differentiation without
+// storing the trajectory).  Every elementary step is the Cayley map
+// U = (1 + i tau H)^{-1} (1 - i tau H), unitary and exactly reversible, so
+// going backward from psi(t_f):
+//   psi_prev = U(-tau) psi   (implicit midpoint with -tau: chi solves
+//              (1 - i tau H) chi = psi, psi_prev = 2 chi - psi),
+//   g_prev   = U^dagger g = U(-tau) g, whose implicit intermediate
+//              mu = (1 - i tau H)^{-1} g is exactly (A^{-1})^dagger g,
+//   dL      += Re(g^H dU psi_prev) = tau Im(mu^H dH (psi + psi_prev)),
+// with dU = -i tau A^{-1} dH (U + 1).  For H = -hbar^2/2m (D + F)^2 + V:
+//   dL/dV_s(q_j)  += tau Im(conj(mu_s) phi_s),  phi = psi + psi_prev,
+//   dL/dF_ab(q_j) += tau Im(-hbar^2/2m [-(conj(nu_a) phi_b - conj(nu_b) phi_a)
+//                                       + (conj(mu_a) u_b - conj(mu_b) u_a)]),
+//   u = (D + F) phi, nu = (D + F) mu.
+// psi is reset to the stored checkpoint at every checkpointed step boundary
+// to bound the reconstruction drift.  g follows the torch convention
+// dL = Re(sum conj(g) dpsi).
+__device__ void run_adjoint(const InstDesc& I, const StepPlan& P, const Smem& sm, qg_step_stats* st, double* red,
+                            double* sc) {
+  const int len = I.S * I.n;
+  const int n = I.n, S = I.S;
+  Dom1D D = make_dom1d(I, sm, P.restart, red);
   double2* psi = I.psi;
+  double2* g = I.grad;
   double2* B = I.work + (size_t)1 * len;
   double2* X = I.work + (size_t)2 * len;
   double2* P0 = I.work + (size_t)3 * len;
-  const HOp<double> H64 = hop64(I, I.work);
+  double2* M = I.work + (size_t)(5 + P.restart) * len;
+  double2* PHI = I.work + (size_t)(6 + P.restart) * len;
+  double2* UU = I.work + (size_t)(7 + P.restart) * len;
+  double2* NU = I.work + (size_t)(8 + P.restart) * len;
   double2* fb = reinterpret_cast<double2*>(sm.fft);
   Counters cnt{0, 0, 0, 0, 0, 0, 0, 0, 0.0};
-  long long nsub = 0;
-  long long failed = -1;
-  vcopy(P0, psi, len);
-  for (long long step = 0; step < P.nsteps && failed < 0; ++step) {
-    for (int f = 0; f < P.nfrac; ++f) {
-      const double tau = 0.5 * P.frac[f] * P.dt;   // hbar = 1
-      const double2 mic = make_double2(0.0, -tau);
-      bool ok;
-      if (P.method == QG_TRAPEZOIDAL) {
-        // b = (1 - i tau H) psi ; guess x0 = (1 - i tau H) b ; solve (1 + i tau H) x = b
-        apply_h_axpby<double>(H64, fb, sm.nb_cap, psi, B, nullptr, 0.0, 1.0, mic);
-        cnt.hpsi += 1;
-        if (mixed) {
-          guess_mixed(I, sm, tau, B, X, cnt);
-          ok = solve_mixed(I, sm, P, tau, B, X, cnt, red, sc);
-        } else {
-          apply_h_axpby<double>(H64, fb, sm.nb_cap, B, X, nullptr, 0.0, 1.0, mic);
-          cnt.hpsi += 1;
-          ok = solve_fp64(I, sm, P, tau, B, X, cnt, red, sc);
-        }
-        if (ok) vcopy(psi, X, len);
-      } else {
-        // guess chi0 = (1 - i tau H) psi ; solve (1 + i tau H) chi = psi ;
-        // psi' = (1 - i tau H) chi  (or 2 chi - psi)
-        if (mixed) {
-          guess_mixed(I, sm, tau, psi, X, cnt);
-          ok = solve_mixed(I, sm, P, tau, psi, X, cnt, red, sc);
-        } else {
-          apply_h_axpby<double>(H64, fb, sm.nb_cap, psi, X, nullptr, 0.0, 1.0, mic);
-          cnt.hpsi += 1;
-          ok = solve_fp64(I, sm, P, tau, psi, X, cnt, red, sc);
-        }
-        if (ok) {
-          if (P.mid_epi) {
-            apply_h_axpby<double>(H64, fb, sm.nb_cap, X, psi, nullptr, 0.0, 1.0, mic);
-            cnt.hpsi += 1;
-          } else {
-            for (int i = threadIdx.x; i < len; i += kThreads) {
-              const double2 c = X[i], p = psi[i];
-              psi[i] = make_double2(2.0 * c.x - p.x, 2.0 * c.y - p.y);
-            }
-            __syncthreads();
-          }
-        }
+  long long nsub = 0, failed = -1;
+  const double h2m = I.h2m;
+  dcopy(D, P0, psi);
+  for (long long step = P.nsteps - 1; step >= 0 && failed < 0; --step) {
+    for (int f = P.nfrac - 1; f >= 0; --f) {
+      const double tau = 0.5 * P.frac[f] * P.dt;
+      const double2 pic = make_double2(0.0, tau);
+      // psi_prev = U(-tau) psi
+      D.hpsi<double>(psi, X, nullptr, 0.0, 1.0, pic);
+      cnt.hpsi++;
+      bool ok = solve_fp64(D, P, -tau, psi, X, cnt, sc);
+      // mu = (1 - i tau H)^{-1} g
+      if (ok) {
+        D.hpsi<double>(g, M, nullptr, 0.0, 1.0, pic);
+        cnt.hpsi++;
+        ok = solve_fp64(D, P, -tau, g, M, cnt, sc);
       }
       if (!ok) {
         failed = step;
         break;
       }
+      for (int i = threadIdx.x; i < len; i += kThreads) {
+        const double2 c = X[i], p = psi[i];
+        const double2 pp = make_double2(2.0 * c.x - p.x, 2.0 * c.y - p.y);
+        B[i] = pp;                                   // psi_prev
+        PHI[i] = make_double2(p.x + pp.x, p.y + pp.y);
+      }
+      __syncthreads();
+      apply_d_plus_f<double>(D.H64, fb, sm.nb_cap, PHI, UU);
+      apply_d_plus_f<double>(D.H64, fb, sm.nb_cap, M, NU);
+      for (int j = threadIdx.x; j < n; j += kThreads) {
+        for (int s = 0; s < S; ++s) {
+          const double2 mu = M[s * n + j], ph = PHI[s * n + j];
+          I.gV[s * n + j] += tau * (mu.x * ph.y - mu.y * ph.x);          // Im(conj(mu) phi)
+        }
+        int pr = 0;
+        for (int a = 0; a < S; ++a)
+          for (int b = a + 1; b < S; ++b) {
+            const double2 na = NU[a * n + j], nb_ = NU[b * n + j];
+            const double2 pa = PHI[a * n + j], pb = PHI[b * n + j];
+            const double2 ma = M[a * n + j], mb = M[b * n + j];
+            const double2 ua = UU[a * n + j], ub = UU[b * n + j];
+            // Im of conj(x) y is x.re y.im - x.im y.re
+            const double t1 = (na.x * pb.y - na.y * pb.x) - (nb_.x * pa.y - nb_.y * pa.x);
+            const double t2 = (ma.x * ub.y - ma.y * ub.x) - (mb.x * ua.y - mb.y * ua.x);
+            I.gF[(size_t)pr * n + j] += tau * (-h2m) * (t2 - t1);
+            ++pr;
+          }
+      }
+      for (int i = threadIdx.x; i < len; i += kThreads) {
+        const double2 m = M[i], gg = g[i];
+        g[i] = make_double2(2.0 * m.x - gg.x, 2.0 * m.y - gg.y);
+        psi[i] = B[i];
+      }
+      __syncthreads();
       nsub++;
     }
+    if (failed < 0 && I.ckpt && step % I.every == 0 && step / I.every < I.nckpt)
+      dcopy(D, psi, I.ckpt + (size_t)(step / I.every) * len);
   }
-  if (failed >= 0) vcopy(psi, P0, len);
-  if (threadIdx.x == 0) {
-    st->n_hpsi = cnt.hpsi;
-    st->n_krylov = cnt.krylov;
-    st->n_substeps = nsub;
-    st->max_krylov = cnt.max_krylov;
-    st->status = failed >= 0 ? QG_ERR_NOT_CONVERGED : QG_OK;
-    st->max_residual = cnt.max_res;
-    st->failed_step = failed;
-    st->n_ortho = cnt.ortho;
-    st->n_update = cnt.update;
-    st->n_restart = cnt.restart;
-    st->n_hpsi32 = cnt.hpsi32;
-    st->n_outer = cnt.outer;
-  }
+  if (failed >= 0) dcopy(D, psi, P0);
+  write_stats(st, cnt, nsub, failed);
 }
 
-__global__ void __launch_bounds__(QG_THREADS, 1)
+// Persistent propagator: CTAs take instances from the work counter.  MINB is
+// the number of CTAs per SM the launch is built for (1: up to 255 registers
+// per thread; 2: 128, twice the warps to hide FP64 latency).
+template <int MINB>
+__global__ void __launch_bounds__(QG_THREADS, MINB)
     propagate_kernel(const InstDesc* __restrict__ insts, int ninst, const StepPlan P, int* counter,
                      qg_step_stats* stats, int max_n, int nb_cap) {
   extern __shared__ __align__(16) unsigned char dyn[];
@@ -485,7 +248,10 @@ __global__ void __launch_bounds__(QG_THREADS, 1)
     __syncthreads();
     if (idx >= ninst) break;
     const InstDesc I = insts[idx];
-    run_instance(I, P, sm, stats + idx, red, sc);
+    if (P.run == QG_RUN_ADJOINT)
+      run_adjoint(I, P, sm, stats + idx, red, sc);
+    else
+      run_instance(I, P, sm, stats + idx, red, sc);
   }
 }
 
@@ -583,20 +349,134 @@ __global__ void __launch_bounds__(QG_THREADS)
 // expression (W12' Delta - W12 Delta') / (W12^2 + Delta^2) is evaluated in the
 // algebraically identical form (dW W12' - W12 dW') / (dW^2 + 4 W12^2),
 // dW = W22 - W11, which has no cancellation where W12 is small.
-__global__ void fields2_kernel(const double* __restrict__ W, const double* __restrict__ dW, int n, double* V,
+__global__ void fields2_kernel(const double* __restrict__ W, const double* __restrict__ dW, int n, int D, double* V,
                                double* F) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const double w11 = W[j], w12 = W[n + j], w22 = W[2 * n + j];
-  const double d11 = dW[j], d12 = dW[n + j], d22 = dW[2 * n + j];
   const double dw = w22 - w11;
   const double wbar = 0.5 * (w11 + w22);
   const double r = hypot(0.5 * dw, w12);
   V[j] = wbar - r;
   V[n + j] = wbar + r;
-  const double ddw = d22 - d11;
-  const double f12 = (dw * d12 - w12 * ddw) / fma(dw, dw, 4.0 * w12 * w12);
-  F[j] = -f12;
+  for (int d = 0; d < D; ++d) {
+    const double* g = dW + (size_t)d * 3 * n;
+    const double d11 = g[j], d12 = g[n + j], d22 = g[2 * n + j];
+    const double ddw = d22 - d11;
+    const double f12 = (dw * d12 - w12 * ddw) / fma(dw, dw, 4.0 * w12 * w12);
+    F[(size_t)d * n + j] = -f12;
+  }
+}
+
+// Adiabatic fields for S >= 2 surfaces (Sec. II E in general form): per grid
+// point the eigen-decomposition W = O diag(V) O^T by cyclic Jacobi rotations
+// (eigenvalues ascending), raw couplings by the Hellmann-Feynman identity
+// F_ij = <phi_i| W' |phi_j> / (V_j - V_i) (= (O^T O')_ij), and the raw
+// eigenvectors for the sign-continuity pass.  W, dW: S(S+1)/2 (x D) upper
+// triangles; out: V (S x n), F (S(S-1)/2 x n), vec (n x S x S, column i =
+// eigenvector i).
+__global__ void fieldsS_eigen_kernel(const double* __restrict__ W, const double* __restrict__ dW, int n, int S,
+                                     double* V, double* F, double* vec) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double a[QG_MAX_S][QG_MAX_S], o[QG_MAX_S][QG_MAX_S], d[QG_MAX_S][QG_MAX_S];
+  int t = 0;
+  for (int r = 0; r < S; ++r)
+    for (int c = r; c < S; ++c) {
+      a[r][c] = a[c][r] = W[(size_t)t * n + j];
+      d[r][c] = d[c][r] = dW[(size_t)t * n + j];
+      ++t;
+    }
+  for (int r = 0; r < S; ++r)
+    for (int c = 0; c < S; ++c) o[r][c] = (r == c) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int r = 0; r < S; ++r) {
+      diag += a[r][r] * a[r][r];
+      for (int c = r + 1; c < S; ++c) off += a[r][c] * a[r][c];
+    }
+    if (off <= 1e-34 * diag || off == 0.0) break;
+    for (int p = 0; p < S - 1; ++p)
+      for (int q = p + 1; q < S; ++q) {
+        if (a[p][q] == 0.0) continue;
+        // rotation zeroing a[p][q] (symmetric Schur decomposition)
+        const double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+        const double tt = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(tt * tt + 1.0), sn = tt * c;
+        for (int k = 0; k < S; ++k) {
+          const double akp = a[k][p], akq = a[k][q];
+          a[k][p] = c * akp - sn * akq;
+          a[k][q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < S; ++k) {
+          const double apk = a[p][k], aqk = a[q][k];
+          a[p][k] = c * apk - sn * aqk;
+          a[q][k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < S; ++k) {
+          const double okp = o[k][p], okq = o[k][q];
+          o[k][p] = c * okp - sn * okq;
+          o[k][q] = sn * okp + c * okq;
+        }
+      }
+  }
+  // ascending order (selection sort on the diagonal)
+  int idx[QG_MAX_S];
+  for (int i = 0; i < S; ++i) idx[i] = i;
+  for (int i = 0; i < S; ++i)
+    for (int k = i + 1; k < S; ++k)
+      if (a[idx[k]][idx[k]] < a[idx[i]][idx[i]]) {
+        const int tmp = idx[i];
+        idx[i] = idx[k];
+        idx[k] = tmp;
+      }
+  for (int i = 0; i < S; ++i) {
+    V[(size_t)i * n + j] = a[idx[i]][idx[i]];
+    for (int r = 0; r < S; ++r) vec[((size_t)j * S + r) * S + i] = o[r][idx[i]];
+  }
+  int pr = 0;
+  for (int i = 0; i < S; ++i)
+    for (int k = i + 1; k < S; ++k) {
+      double num = 0.0;
+      for (int r = 0; r < S; ++r)
+        for (int c = 0; c < S; ++c) num += o[r][idx[i]] * d[r][c] * o[c][idx[k]];
+      F[(size_t)pr * n + j] = num / (a[idx[k]][idx[k]] - a[idx[i]][idx[i]]);
+      ++pr;
+    }
+}
+
+// Sign gauge along the grid: at the first point each eigenvector's largest
+// component is made positive; afterwards each eigenvector is flipped when its
+// overlap with the (already fixed) eigenvector at the previous point is
+// negative.  One thread per model walks the grid (pre-processing, once per
+// model); the couplings are rescaled by the product of the two signs.
+__global__ void fieldsS_gauge_kernel(int n, int S, double* F, double* vec) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int j = 0; j < n; ++j) {
+    double sg[QG_MAX_S];
+    for (int i = 0; i < S; ++i) {
+      double* v = vec + (size_t)j * S * S;
+      double dot = 0.0;
+      if (j == 0) {
+        int big = 0;
+        for (int r = 1; r < S; ++r)
+          if (fabs(v[r * S + i]) > fabs(v[big * S + i])) big = r;
+        dot = v[big * S + i];
+      } else {
+        const double* u = vec + (size_t)(j - 1) * S * S;
+        for (int r = 0; r < S; ++r) dot += v[r * S + i] * u[r * S + i];
+      }
+      sg[i] = dot < 0.0 ? -1.0 : 1.0;
+      if (sg[i] < 0.0)
+        for (int r = 0; r < S; ++r) v[r * S + i] = -v[r * S + i];
+    }
+    int pr = 0;
+    for (int i = 0; i < S; ++i)
+      for (int k = i + 1; k < S; ++k) {
+        F[(size_t)pr * n + j] *= sg[i] * sg[k];
+        ++pr;
+      }
+  }
 }
 
 __global__ void to_f32_kernel(const double* __restrict__ in, float* out, size_t n) {
@@ -609,12 +489,13 @@ __global__ void to_f32_kernel(const double* __restrict__ in, float* out, size_t 
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers.
 
-static int nb_capacity(int max_n, int max_S, int restart, size_t* bytes_out) {
+static int nb_capacity(int max_n, int max_S, int restart, size_t* bytes_out, size_t budget = 200 * 1024,
+                       int force_nb = 0) {
   // one or all surfaces' FFT buffers, whichever fits next to the GMRES arrays
-  const size_t budget = 200 * 1024;
-  const size_t rest = (size_t)(restart + 1) * restart * 16 + (size_t)(restart + 1) * 16 + (size_t)restart * 40 + 256;
+  const size_t rest = qg::gmres_smem_bytes(restart);
   int nb = max_S;
   if ((size_t)max_S * max_n * 16 + rest > budget) nb = 1;
+  if (force_nb > 0 && force_nb < nb) nb = force_nb;
   if (bytes_out) *bytes_out = (size_t)nb * max_n * 16 + rest + 64;
   return nb;
 }
@@ -625,20 +506,34 @@ size_t qg_smem_bytes(int max_n, int max_S, int restart) {
   return b;
 }
 
-cudaError_t qg_launch_propagate(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
-                                qg_step_stats* d_stats, int max_n, int max_S, cudaStream_t st) {
+cudaError_t qg_launch_propagate_tuned(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
+                                      qg_step_stats* d_stats, int max_n, int max_S, int ctas_per_sm, int nb_pref,
+                                      cudaStream_t st) {
   size_t smem;
-  const int nb = nb_capacity(max_n, max_S, plan.restart, &smem);
-  cudaError_t e = cudaFuncSetAttribute(qg::propagate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t budget = ctas_per_sm >= 2 ? 110 * 1024 : 200 * 1024;
+  const int nb = nb_capacity(max_n, max_S, plan.restart, &smem, budget, nb_pref);
+  if (smem > budget + 1024) return cudaErrorInvalidConfiguration;
+  const void* fn = ctas_per_sm >= 2 ? (const void*)qg::propagate_kernel<2> : (const void*)qg::propagate_kernel<1>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if (ninst == 0) return cudaSuccess;   // attributes only
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = ninst < sms ? ninst : sms;
+  const int slots = sms * (ctas_per_sm >= 2 ? 2 : 1);
+  const int grid = ninst < slots ? ninst : slots;
   e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  qg::propagate_kernel<<<grid, QG_THREADS, smem, st>>>(d_insts, ninst, plan, d_counter, d_stats, max_n, nb);
+  if (ctas_per_sm >= 2)
+    qg::propagate_kernel<2><<<grid, QG_THREADS, smem, st>>>(d_insts, ninst, plan, d_counter, d_stats, max_n, nb);
+  else
+    qg::propagate_kernel<1><<<grid, QG_THREADS, smem, st>>>(d_insts, ninst, plan, d_counter, d_stats, max_n, nb);
   return cudaGetLastError();
+}
+
+cudaError_t qg_launch_propagate(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
+                                qg_step_stats* d_stats, int max_n, int max_S, cudaStream_t st) {
+  return qg_launch_propagate_tuned(d_insts, ninst, plan, d_counter, d_stats, max_n, max_S, 1, 0, st);
 }
 
 cudaError_t qg_launch_apply_h(const InstDesc* d_inst, double2* d_out, int n, int S, cudaStream_t st) {
@@ -682,9 +577,18 @@ cudaError_t qg_launch_to_f32(const double* d_in, float* d_out, size_t n, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t qg_launch_fields2(const double* d_W, const double* d_dW, int n, double* d_V, double* d_F,
+cudaError_t qg_launch_fieldsS(const double* d_W, const double* d_dW, int n, int S, double* d_V, double* d_F,
+                              double* d_vec, cudaStream_t st) {
+  qg::fieldsS_eigen_kernel<<<(n + 127) / 128, 128, 0, st>>>(d_W, d_dW, n, S, d_V, d_F, d_vec);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  qg::fieldsS_gauge_kernel<<<1, 32, 0, st>>>(n, S, d_F, d_vec);
+  return cudaGetLastError();
+}
+
+cudaError_t qg_launch_fields2(const double* d_W, const double* d_dW, int n, int D, double* d_V, double* d_F,
                               cudaStream_t st) {
-  qg::fields2_kernel<<<(n + 255) / 256, 256, 0, st>>>(d_W, d_dW, n, d_V, d_F);
+  qg::fields2_kernel<<<(n + 255) / 256, 256, 0, st>>>(d_W, d_dW, n, D, d_V, d_F);
   return cudaGetLastError();
 }
 
@@ -773,6 +677,12 @@ __global__ void __launch_bounds__(QG_THREADS, 1)
   I.V32 = nullptr;
   I.F32 = nullptr;
   I.work32 = nullptr;
+  I.ckpt = nullptr;
+  I.nckpt = 0;
+  I.every = 1;
+  I.grad = nullptr;
+  I.gV = nullptr;
+  I.gF = nullptr;
   qg_step_stats* st = reinterpret_cast<qg_step_stats*>(base + kNaWorkBytes + kNaTwBytes + kNaKdBytes);
   const Smem sm = carve_smem(dyn, in.n, nb_cap, P.restart);
   run_instance(I, P, sm, st, red, sc);

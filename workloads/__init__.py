@@ -15,3 +15,4 @@ from .constants import (AU_TIME_PER_FS, NAI_REDUCED_MASS, NAI_QMIN, NAI_QMAX,
 from .nai_like import nai_like_diabatic, nai_like_params, initial_gaussian_params
 from .random_inputs import random_psi, random_adiabatic_fields
 from .avoided_crossing import avoided_crossing_model
+from .model2d import PARAMS as MODEL2D_PARAMS, model2d_diabatic, model2d_initial
