@@ -566,6 +566,9 @@ def run_adjoint(args):
 # the cheapest point of the coarse sweep, refined: Suzuki order 8 around
 # dt = t_f / 1024
 SWEEP_VERIFY = {(1, 8): [768, 1024, 1536, 2048]}
+# one propagation at the operating point, compared offline with the
+# n = 2048 run of the verify set
+SWEEP_POINT = {(1, 8): [1024]}
 
 
 def run_sweep(args):
@@ -589,7 +592,7 @@ def run_sweep(args):
     W, dW = wl.nai_like_diabatic(grid.points())
     model = qg.Model(grid, 2, [wl.NAI_REDUCED_MASS], W=W, dW=dW)
     prec = qg.QG_C64_MIXED if args.precision == "mixed" else qg.QG_C128
-    table = SWEEP_VERIFY if args.sweep_set == "verify" else SWEEP_JOBS
+    table = {"verify": SWEEP_VERIFY, "coarse": SWEEP_JOBS, "point": SWEEP_POINT}[args.sweep_set]
     jobs = [(sc, o, n) for (sc, o), ns in table.items() for n in ns]
     jobs.sort(key=lambda j: -j[2] * (3 if j[0] == 0 else 5) ** (j[1] // 2 - 1))
     opts = qg.default_solver_opts(tol=args.sweep_tol, max_iters=600,
@@ -643,14 +646,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="convergence-error sweep that fixes the operating point")
-    ap.add_argument("--solver", default="gmres", choices=["gmres", "lanczos"])
+    ap.add_argument("--solver", default="lanczos", choices=["gmres", "lanczos"],
+                    help="Krylov method of the implicit steps (same minimal-residual iterates)")
     ap.add_argument("--workload", default="nai", choices=["nai", "batched", "2d", "adjoint"])
     ap.add_argument("--models", type=int, default=0)
     ap.add_argument("--per-instance-sample", type=int, default=64)
     ap.add_argument("--tf", type=float, default=10500.0)
     ap.add_argument("--sweep-tol", type=float, default=1e-15)
     ap.add_argument("--sweep-dir", default="")
-    ap.add_argument("--sweep-set", default="verify", choices=["verify", "coarse"])
+    ap.add_argument("--sweep-set", default="verify", choices=["verify", "coarse", "point"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every Krylov iteration in FP64; mixed: complex64 inner solves, FP64 refinement")
     args = ap.parse_args()

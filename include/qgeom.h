@@ -313,6 +313,13 @@ qg_status qg_propagate_noalloc(int N, double qmin, double qmax, int S, double ma
                                int64_t nsteps, const qg_solver_opts* opts, qg_step_stats* stats,
                                void* stream);
 
+/* Failure-path self-test of the bounded grid barrier used by 2-D grids (not
+ * in the paper): a small cooperative launch in which one CTA never arrives;
+ * every other CTA must give up after its wait limit (about a second), raise
+ * the error flag and leave.  Returns QG_ERR_TIMEOUT with *timed_out = 1 and
+ * *passed = 0 when the time-out path works. */
+qg_status qg_selftest_barrier_timeout(int* timed_out, int* passed);
+
 /* Human-readable name of a status; message of the last CUDA error seen by
  * this thread. */
 const char* qg_status_string(qg_status st);

@@ -42,7 +42,7 @@ EXPORTED = [
     "qg_destroy_state", "qg_state_set_stream", "qg_set_state", "qg_get_state", "qg_set_gaussian",
     "qg_apply_h", "qg_step_implicit", "qg_propagate", "qg_norm", "qg_energy", "qg_population",
     "qg_overlap", "qg_batch_propagate", "qg_batch_create", "qg_batch_run", "qg_batch_capture", "qg_batch_replay", "qg_batch_stats",
-    "qg_batch_stream", "qg_batch_destroy", "qg_batch_autotune", "qg_batch_tuning", "qg_state_set_adjoint", "qg_propagate_ex", "qg_batch_run_ex", "qg_propagate_noalloc", "qg_status_string", "qg_last_error_string", "qg_version",
+    "qg_batch_stream", "qg_batch_destroy", "qg_batch_autotune", "qg_batch_tuning", "qg_selftest_barrier_timeout", "qg_state_set_adjoint", "qg_propagate_ex", "qg_batch_run_ex", "qg_propagate_noalloc", "qg_status_string", "qg_last_error_string", "qg_version",
 ]
 
 
@@ -119,6 +119,7 @@ def lib():
             "qg_batch_autotune": (I, [P, I, I, I, D, ctypes.c_int64, ctypes.POINTER(SolverOpts),
                                       ctypes.POINTER(ctypes.c_double)]),
             "qg_batch_tuning": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+            "qg_selftest_barrier_timeout": (I, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
             "qg_batch_destroy": (V, [P]),
             "qg_state_set_adjoint": (I, [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P]),
             "qg_propagate_ex": (I, [P, I, I, I, I, D, ctypes.c_int64, ctypes.POINTER(SolverOpts),

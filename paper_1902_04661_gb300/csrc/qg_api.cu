@@ -1035,4 +1035,16 @@ qg_status qg_propagate_noalloc(int N, double qmin, double qmax, int S, double ma
   return (qg_status)h.status;
 }
 
+qg_status qg_selftest_barrier_timeout(int* timed_out, int* passed) {
+  int* d = nullptr;
+  QG_TRY(cudaMalloc(&d, 4 * sizeof(int)));
+  cudaError_t e = qg_selftest_barrier(d, timed_out, passed);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    set_err("qg_selftest_barrier_timeout", e);
+    return QG_ERR_CUDA;
+  }
+  return (timed_out && *timed_out) ? QG_ERR_TIMEOUT : QG_OK;
+}
+
 }  // extern "C"

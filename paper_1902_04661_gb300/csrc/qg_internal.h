@@ -195,6 +195,7 @@ cudaError_t qg_launch_apply_h2d(const Inst2D& I, double2* d_out, double* d_energ
 cudaError_t qg_launch_gaussian2d(double2* d_psi, const int* n, int S, int surface, const double* qmin,
                                  const double* dq, const double* q0, const double* p0, const double* s0,
                                  cudaStream_t st);
+cudaError_t qg_selftest_barrier(int* d_words, int* h_timed_out, int* h_passed);
 cudaError_t qg_launch_to_f32(const double* d_in, float* d_out, size_t n, cudaStream_t st);
 cudaError_t qg_launch_fieldsS(const double* d_W, const double* d_dW, int n, int S, double* d_V, double* d_F,
                               double* d_vec, cudaStream_t st);

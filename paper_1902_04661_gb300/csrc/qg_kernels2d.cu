@@ -40,6 +40,10 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
           atomicExch(err, 1);
           break;
         }
+        if (*(volatile int*)err) {   // another CTA already gave up
+          fail = 1;
+          break;
+        }
         __nanosleep(64);
       }
     }
@@ -344,7 +348,37 @@ __global__ void __launch_bounds__(QG_THREADS)
     }
 }
 
+// Failure-path check of grid_barrier: CTA `absent` never arrives, so every
+// other CTA's wait must run out, raise the flag and return false.
+__global__ void barrier_timeout_kernel(unsigned* bar, int* err, int absent, int* ok_count) {
+  if ((int)blockIdx.x == absent) return;
+  const bool ok = grid_barrier(bar, err);
+  if (threadIdx.x == 0 && ok) atomicAdd(ok_count, 1);
+}
+
 }  // namespace qg
+
+cudaError_t qg_selftest_barrier(int* d_words, int* h_timed_out, int* h_passed) {
+  // d_words: 4 ints of device scratch (count, generation, error flag, passes)
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int G = sms < 8 ? sms : 8;
+  cudaError_t e = cudaMemset(d_words, 0, 4 * sizeof(int));
+  if (e != cudaSuccess) return e;
+  unsigned* bar = reinterpret_cast<unsigned*>(d_words);
+  int* err = d_words + 2;
+  int* okc = d_words + 3;
+  int absent = 0;
+  void* args[] = {&bar, &err, &absent, &okc};
+  e = cudaLaunchCooperativeKernel((const void*)qg::barrier_timeout_kernel, dim3(G), dim3(32), args, 0, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int h[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, d_words, sizeof(h), cudaMemcpyDeviceToHost);
+  if (h_timed_out) *h_timed_out = h[2];
+  if (h_passed) *h_passed = h[3];
+  return e;
+}
 
 static size_t fft2d_bytes(const Inst2D& I) {
   const int nmax = I.n[0] > I.n[1] ? I.n[0] : I.n[1];
