@@ -136,6 +136,24 @@ def fp64_peak_tflops(sm_mhz=None):
     return 152 * 4 * mhz * 1e6 / 1e12
 
 
+def shard_seeds(rank, per_rank):
+    """Seeds of the wavepackets rank `rank` propagates (weak scaling: every
+    rank owns per_rank independent wavepackets; no data is exchanged)."""
+    return [rank * per_rank + i for i in range(per_rank)]
+
+
+def max_over_ranks(value, device=None):
+    """Largest value over all ranks (the job time is the slowest rank's);
+    the single collective of a multi-GPU run, on timing only."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _setup_batch(qg, wl, B, rank, stream, precision=0):
     N = WORKLOAD["N"]
     grid = qg.Grid([N], [wl.NAI_QMIN], [wl.NAI_QMAX])
@@ -143,9 +161,9 @@ def _setup_batch(qg, wl, B, rank, stream, precision=0):
     W, dW = wl.nai_like_diabatic(q)
     model = qg.Model(grid, 2, [wl.NAI_REDUCED_MASS], W=W, dW=dW)
     states = []
-    for i in range(B):
+    for seed in shard_seeds(rank, B):
         st = qg.State(model, precision=precision, stream=stream)
-        q0, p0, s0 = wl.initial_gaussian_params(rank * B + i)
+        q0, p0, s0 = wl.initial_gaussian_params(seed)
         st.set_gaussian(1, [q0], [p0], [s0])
         states.append(st)
     return grid, model, states
@@ -177,6 +195,7 @@ def run_ours(args):
     dt = WORKLOAD["dt_fs"] * FS
     m, o, sc = WORKLOAD["method"], WORKLOAD["order"], WORKLOAD["scheme"]
     N, S = WORKLOAD["N"], WORKLOAD["S"]
+    tuning = batch.autotune(m, o, sc, dt, 1, opts) if not args.no_autotune else None
     for _ in range(args.warmup):
         batch.run(m, o, sc, dt, 1, opts)
     torch.cuda.synchronize()
@@ -195,9 +214,7 @@ def run_ours(args):
     launch_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     t_ms = sum(launch_ms)
     if world > 1:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+        t_ms = max_over_ranks(t_ms, "cuda")
         dist.barrier()
     flat = [s for st in stats_all for s in st]
     n_hpsi = sum(s["n_hpsi"] for s in flat)
@@ -235,9 +252,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e_ms = e0.elapsed_time(e1)
     if world > 1:
-        tt = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_ms = float(tt.item())
+        e_ms = max_over_ranks(e_ms, "cuda")
     e2e = B * e_steps * world / (e_ms / 1e3)
 
     if rank == 0:
@@ -266,6 +281,7 @@ def run_ours(args):
                          "kernel": "qg::propagate_kernel",
                          "peak_source": "FP64 FMA peak 152 SMs x 4 flop/clk x 2070 MHz (measured 2 DFMA/SM/clk)"},
             "gpu_launches": args.steps,
+            "autotune": tuning,
             "clocks": clocks,
             "e2e": {"value": e2e, "unit": "wavepacket-steps/s", "h2d_bytes_per_step": B * len_state * 16,
                     "d2h_bytes_per_step": B * len_state * 16},
@@ -470,7 +486,8 @@ def run_2d(args):
     m = qg.Model(g, 2, list(p["mass"]), W=W, dW=dW)
     q0, p0, s0 = wl.model2d_initial()
     dt = 0.1 * FS
-    opts = qg.default_solver_opts(tol=1e-12)
+    opts = qg.default_solver_opts(tol=1e-12,
+                                  solver=qg.QG_SOLVER_LANCZOS if args.solver == "lanczos" else qg.QG_SOLVER_GMRES)
     res = {}
     for name, prec in (("mixed", qg.QG_C64_MIXED), ("fp64", qg.QG_C128)):
         st = qg.State(m, precision=prec)
@@ -494,7 +511,8 @@ def run_2d(args):
             "scaling": "strong", "vs_baseline": None, "dtype": "c64 inner / f64 residual",
             "data": "synthetic (2-D two-state model)",
             "config": {"workload": "model2d_256x256_midpoint_suzuki6", "grid": list(ns), "S": 2, "order": 6,
-                       "dt_fs": 0.1, "gmres_tol": 1e-12, "launch": "one cooperative launch over all SMs"},
+                       "dt_fs": 0.1, "gmres_tol": 1e-12, "solver": args.solver,
+                       "launch": "one cooperative launch over all SMs"},
             "fp64_path": {"value": args.steps / (t_f / 1e3), "ms_per_step": t_f / args.steps,
                           "fp64_hpsi": res["fp64"]["stats"]["n_hpsi"]},
             "speedup_mixed_over_fp64": t_f / t_m,
@@ -540,7 +558,8 @@ def run_adjoint(args):
     st.set_gaussian(1, [wl.NAI_Q0], [0.0], [wl.NAI_SIGMA0])
     psi0 = torch.tensor(np.stack([st.get()] * nm), device="cuda", requires_grad=True)
     dt, nsteps = 0.5 * FS, args.steps
-    opts = qg.default_solver_opts(tol=1e-12)
+    opts = qg.default_solver_opts(tol=1e-12,
+                                  solver=qg.QG_SOLVER_LANCZOS if args.solver == "lanczos" else qg.QG_SOLVER_GMRES)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e2 = torch.cuda.Event(enable_timing=True)
@@ -552,13 +571,22 @@ def run_adjoint(args):
     L.backward()
     e2.record()
     torch.cuda.synchronize()
-    tf, tb = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    tf, tb = qad.last_stats["forward_ms"], qad.last_stats["adjoint_ms"]
+
+    def agg(key):
+        st = qad.last_stats[key]
+        sub = sum(x["n_substeps"] for x in st)
+        return {"substeps": sub, "hpsi_per_substep": sum(x["n_hpsi"] for x in st) / max(1, sub),
+                "krylov_per_substep": sum(x["n_krylov"] for x in st) / max(1, sub),
+                "restarts": sum(x["n_restart"] for x in st)}
     line = {"metric": METRIC, "value": nm * nsteps / ((tf + tb) / 1e3), "unit": "wavepacket-steps/s (forward+adjoint)",
             "n_gpus": 1, "steps": nsteps, "warmup": 0, "ms_per_step": (tf + tb) / nsteps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (perturbed NaI-like models)",
             "config": {"workload": "nai_like_adjoint_x%d_n2048_suzuki4" % nm, "models": nm, "N": N, "order": 4,
                        "dt_fs": 0.5, "checkpoint_every": 8},
             "forward_ms": tf, "adjoint_ms": tb, "adjoint_over_forward": tb / tf,
+            "forward_stats": agg("forward"), "adjoint_stats": agg("adjoint"),
+            "wall_ms_incl_setup": e0.elapsed_time(e2),
             "grad_norms": {"V": float(V.grad.norm()), "F": float(F.grad.norm()), "psi0": float(psi0.grad.norm())}}
     print(json.dumps(line), flush=True)
 
@@ -645,6 +673,7 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="wavepackets per GPU (default: one per SM)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="convergence-error sweep that fixes the operating point")
     ap.add_argument("--solver", default="lanczos", choices=["gmres", "lanczos"],
                     help="Krylov method of the implicit steps (same minimal-residual iterates)")

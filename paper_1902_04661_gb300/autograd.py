@@ -15,6 +15,24 @@ import torch
 
 from . import _binding as B
 
+# statistics of the most recent batched forward and adjoint launches:
+# {"forward": [per-instance stats], "forward_ms": launch time, "adjoint": [...], "adjoint_ms": ...}
+last_stats = {}
+
+
+def _timed_batch_run(batch, run, method, order, scheme, dt, nsteps, opts, n):
+    stt, sts = (ctypes.c_int32 * n)(), (B.StepStats * n)()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.ExternalStream(B.lib().qg_batch_stream(batch.handle))
+    e0.record(stream)
+    r = B.lib().qg_batch_run_ex(batch.handle, run, method, order, scheme, float(dt), int(nsteps), ctypes.byref(opts),
+                                stt, sts)
+    e1.record(stream)
+    B._check(r, "qg_batch_run_ex")
+    e1.synchronize()
+    return [x.as_dict() for x in sts], e0.elapsed_time(e1)
+
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
@@ -87,11 +105,9 @@ class PropagateBatch(torch.autograd.Function):
         opts = opts if opts is not None else B.default_solver_opts()
         runs = [_Run(grid, V[b], F[b], psi0[b], mass, nsteps, every) for b in range(psi0.shape[0])]
         batch = B.Batch([r.state for r in runs])
-        st = B.StepStats * len(runs)
-        stt, sts = (ctypes.c_int32 * len(runs))(), st()
-        r = B.lib().qg_batch_run_ex(batch.handle, B.QG_RUN_CHECKPOINT, method, order, scheme, float(dt), int(nsteps),
-                                    ctypes.byref(opts), stt, sts)
-        B._check(r, "qg_batch_run_ex")
+        stats, ms = _timed_batch_run(batch, B.QG_RUN_CHECKPOINT, method, order, scheme, dt, nsteps, opts, len(runs))
+        last_stats.clear()
+        last_stats.update(forward=stats, forward_ms=ms)
         out = torch.empty_like(psi0)
         for b, run in enumerate(runs):
             run.state.get(out[b])
@@ -106,11 +122,10 @@ class PropagateBatch(torch.autograd.Function):
             run.grad.copy_(g_out[b].contiguous())
             run.gV.zero_()
             run.gF.zero_()
-        n = len(ctx.runs)
-        stt, sts = (ctypes.c_int32 * n)(), (B.StepStats * n)()
-        r = B.lib().qg_batch_run_ex(ctx.batch.handle, B.QG_RUN_ADJOINT, method, order, scheme, float(dt), int(nsteps),
-                                    ctypes.byref(opts), stt, sts)
-        B._check(r, "qg_batch_run_ex")
+        torch.cuda.synchronize()
+        stats, ms = _timed_batch_run(ctx.batch, B.QG_RUN_ADJOINT, method, order, scheme, dt, nsteps, opts,
+                                     len(ctx.runs))
+        last_stats.update(adjoint=stats, adjoint_ms=ms)
         gV = torch.stack([r_.gV for r_ in ctx.runs])
         gF = torch.stack([r_.gF for r_ in ctx.runs])
         gpsi = torch.stack([r_.grad for r_ in ctx.runs])

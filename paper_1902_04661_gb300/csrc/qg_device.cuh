@@ -66,6 +66,19 @@ __device__ __forceinline__ C mul_i(C a) { return cmk<C>(-a.y, a.x); }
 
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 
+// Shared-memory FFT buffers are padded with one element after every 8
+// (complex128) or 16 (complex64) elements: the strided butterfly accesses of
+// the late passes then spread over the banks instead of hitting a few.
+template <typename C>
+__device__ __forceinline__ int spad(int e) {
+  return e + (e >> (sizeof(C) == 16 ? 3 : 4));
+}
+// Bytes of a padded buffer of `elems` complex values of `elem_bytes` each.
+__host__ __device__ inline size_t padded_bytes(size_t elems, size_t elem_bytes) {
+  const size_t e = elems + (elems >> (elem_bytes == 16 ? 3 : 4)) + 1;
+  return ((e * elem_bytes) + 15) & ~size_t(15);
+}
+
 // ---------------------------------------------------------------------------
 // Deterministic CTA-wide sums of K values per thread.  The xor-butterfly
 // leaves bitwise identical sums in every lane; warps are then added in a
@@ -200,10 +213,10 @@ __device__ __forceinline__ void fft_pass(C* buf, int n, int nb, int L, const C* 
     const int bb = b & ((n / RD) - 1);
     const int blk = bb >> lm;
     const int j = bb & (m - 1);
-    C* p = buf + v * n + blk * L + j;
+    const int e0 = v * n + blk * L + j;
     C x[RD];
 #pragma unroll
-    for (int r = 0; r < RD; ++r) x[r] = p[r * m];
+    for (int r = 0; r < RD; ++r) x[r] = buf[spad<C>(e0 + r * m)];
     if (!INV) {
       dft<RD, false>(x);
       if (j) {
@@ -218,7 +231,7 @@ __device__ __forceinline__ void fft_pass(C* buf, int n, int nb, int L, const C* 
       dft<RD, true>(x);
     }
 #pragma unroll
-    for (int r = 0; r < RD; ++r) p[r * m] = x[r];
+    for (int r = 0; r < RD; ++r) buf[spad<C>(e0 + r * m)] = x[r];
   }
 }
 
@@ -228,11 +241,11 @@ template <int RD, typename C, typename R>
 __device__ __forceinline__ void fft_center(C* buf, int n, int nb, const R* __restrict__ kd) {
   const int total = (nb * n) / RD;
   for (int b = threadIdx.x; b < total; b += kThreads) {
-    C* p = buf + b * RD;
-    const int pos = (b * RD) & (n - 1);
+    const int e0 = b * RD;
+    const int pos = e0 & (n - 1);
     C x[RD];
 #pragma unroll
-    for (int r = 0; r < RD; ++r) x[r] = p[r];
+    for (int r = 0; r < RD; ++r) x[r] = buf[spad<C>(e0 + r)];
     dft<RD, false>(x);
 #pragma unroll
     for (int r = 0; r < RD; ++r) {
@@ -241,7 +254,7 @@ __device__ __forceinline__ void fft_center(C* buf, int n, int nb, const R* __res
     }
     dft<RD, true>(x);
 #pragma unroll
-    for (int r = 0; r < RD; ++r) p[r] = x[r];
+    for (int r = 0; r < RD; ++r) buf[spad<C>(e0 + r)] = x[r];
   }
 }
 
@@ -313,12 +326,12 @@ __device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T
   const int nb = (S <= nb_cap) ? S : 1;
   // U = (D + F) x
   for (int s0 = 0; s0 < S; s0 += nb) {
-    for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[i] = x[s0 * n + i];
+    for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[spad<C>(i)] = x[s0 * n + i];
     __syncthreads();
     spectral_derivative<R>(sbuf, nb, H);
     for (int i = threadIdx.x; i < nb * n; i += kThreads) {
       const int s = s0 + (i >> ln), j = i & (n - 1);
-      C acc = sbuf[i];
+      C acc = sbuf[spad<C>(i)];
       for (int t = 0; t < S; ++t)
         if (t != s) acc = caxpy_r(coupling(H, s, t, j), x[t * n + j], acc);
       U[s * n + j] = acc;
@@ -328,12 +341,12 @@ __device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T
   // y = e z + a x + c (-hbar^2/2m (D + F) U + V x)
   const R mh = -H.h2m;
   for (int s0 = 0; s0 < S; s0 += nb) {
-    for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[i] = U[s0 * n + i];
+    for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[spad<C>(i)] = U[s0 * n + i];
     __syncthreads();
     spectral_derivative<R>(sbuf, nb, H);
     for (int i = threadIdx.x; i < nb * n; i += kThreads) {
       const int s = s0 + (i >> ln), j = i & (n - 1);
-      C acc = sbuf[i];
+      C acc = sbuf[spad<C>(i)];
       for (int t = 0; t < S; ++t)
         if (t != s) acc = caxpy_r(coupling(H, s, t, j), U[t * n + j], acc);
       const C xs = x[s * n + j];
@@ -357,12 +370,12 @@ __device__ __forceinline__ void apply_d_plus_f(const HOp<R>& H, typename Cx<R>::
   const int ln = ilog2(n);
   const int nb = (S <= nb_cap) ? S : 1;
   for (int s0 = 0; s0 < S; s0 += nb) {
-    for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[i] = x[s0 * n + i];
+    for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[spad<C>(i)] = x[s0 * n + i];
     __syncthreads();
     spectral_derivative<R>(sbuf, nb, H);
     for (int i = threadIdx.x; i < nb * n; i += kThreads) {
       const int s = s0 + (i >> ln), j = i & (n - 1);
-      C acc = sbuf[i];
+      C acc = sbuf[spad<C>(i)];
       for (int t = 0; t < S; ++t)
         if (t != s) acc = caxpy_r(coupling(H, s, t, j), x[t * n + j], acc);
       y[s * n + j] = acc;

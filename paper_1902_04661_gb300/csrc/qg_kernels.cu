@@ -23,7 +23,7 @@ __device__ Smem carve_smem(void* base, int max_n, int nb_cap, int m) {
   Smem s;
   unsigned char* p = reinterpret_cast<unsigned char*>(base);
   s.fft = p;
-  s.gm = p + align16(sizeof(double2) * (size_t)nb_cap * max_n);
+  s.gm = p + padded_bytes((size_t)nb_cap * max_n, sizeof(double2));
   s.nb_cap = nb_cap;
   s.m = m;
   return s;
@@ -494,9 +494,9 @@ static int nb_capacity(int max_n, int max_S, int restart, size_t* bytes_out, siz
   // one or all surfaces' FFT buffers, whichever fits next to the GMRES arrays
   const size_t rest = qg::gmres_smem_bytes(restart);
   int nb = max_S;
-  if ((size_t)max_S * max_n * 16 + rest > budget) nb = 1;
+  if (qg::padded_bytes((size_t)max_S * max_n, 16) + rest > budget) nb = 1;
   if (force_nb > 0 && force_nb < nb) nb = force_nb;
-  if (bytes_out) *bytes_out = (size_t)nb * max_n * 16 + rest + 64;
+  if (bytes_out) *bytes_out = qg::padded_bytes((size_t)nb * max_n, 16) + rest + 64;
   return nb;
 }
 

@@ -72,6 +72,7 @@ struct Dom2D {
   float2 *r32, *d32, *basis32;
   int parity;
   bool good;
+  int cap_elems;   // complex values one shared-memory FFT batch may hold
 
   template <class F>
   __device__ __forceinline__ void each(F&& f) {
@@ -127,88 +128,101 @@ struct Dom2D {
       F = I->F32;
     }
     const int npair = S * (S - 1) / 2;
-    // ---- dimension 1 (rows, contiguous): T = -h2m_1 (D_1 + F_1)^2 x + V x
+    // ---- dimension 1 (rows, contiguous): T = -h2m_1 (D_1 + F_1)^2 x + V x.
+    // All owned rows and all surfaces form one shared-memory FFT batch:
+    // vector (row_local * S + s) holds x_s on that row.
     {
       const HOp<R>& H1 = H[1];
       const R mh = -(R)I->h2m[1];
       const R* F1 = F + (size_t)1 * npair * N;
-      for (int r = r_lo; r < r_hi; ++r) {
-        for (int k = threadIdx.x; k < S * n1; k += kThreads) {
-          const int s = k / n1, j = k - s * n1;
-          sb[k] = x[(size_t)s * N + (size_t)r * n1 + j];
+      const int rb = max(1, min(r_hi - r_lo, cap_elems / (S * n1)));
+      for (int r0 = r_lo; r0 < r_hi; r0 += rb) {
+      const int nrow = min(rb, r_hi - r0);
+      const int nv = nrow * S;
+      for (int k = threadIdx.x; k < nv * n1; k += kThreads) {
+        const int v = k / n1, j = k - v * n1;
+        const int rl = v / S, s = v - rl * S;
+        sb[spad<C>(k)] = x[(size_t)s * N + (size_t)(r0 + rl) * n1 + j];
+      }
+      __syncthreads();
+      if (nv > 0) spectral_derivative<R>(sb, nv, H1);
+      for (int k = threadIdx.x; k < nrow * n1; k += kThreads) {
+        const int rl = k / n1, j = k - rl * n1;
+        const size_t p = (size_t)(r0 + rl) * n1 + j;
+        for (int s = 0; s < S; ++s) {
+          const int e = (rl * S + s) * n1 + j;
+          C acc = sb[spad<C>(e)];
+          for (int t = 0; t < S; ++t)
+            if (t != s) acc = caxpy_r(coupling2(F1, N, S, s, t, p), x[(size_t)t * N + p], acc);
+          U[(size_t)s * N + p] = acc;
+          sb[spad<C>(e)] = acc;
         }
-        __syncthreads();
-        spectral_derivative<R>(sb, S, H1);
-        for (int k = threadIdx.x; k < n1; k += kThreads) {
-          const size_t p = (size_t)r * n1 + k;
-          for (int s = 0; s < S; ++s) {
-            C acc = sb[s * n1 + k];
-            for (int t = 0; t < S; ++t)
-              if (t != s) acc = caxpy_r(coupling2(F1, N, S, s, t, p), x[(size_t)t * N + p], acc);
-            U[(size_t)s * N + p] = acc;
-          }
+      }
+      __syncthreads();
+      if (nv > 0) spectral_derivative<R>(sb, nv, H1);
+      for (int k = threadIdx.x; k < nrow * n1; k += kThreads) {
+        const int rl = k / n1, j = k - rl * n1;
+        const size_t p = (size_t)(r0 + rl) * n1 + j;
+        for (int s = 0; s < S; ++s) {
+          C acc = sb[spad<C>((rl * S + s) * n1 + j)];
+          for (int t = 0; t < S; ++t)
+            if (t != s) acc = caxpy_r(coupling2(F1, N, S, s, t, p), U[(size_t)t * N + p], acc);
+          const C xs = x[(size_t)s * N + p];
+          const R v = __ldg(V + (size_t)s * N + p);
+          T[(size_t)s * N + p] = cmk<C>(fma(mh, acc.x, v * xs.x), fma(mh, acc.y, v * xs.y));
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < S * n1; k += kThreads) {
-          const int s = k / n1, j = k - s * n1;
-          sb[k] = U[(size_t)s * N + (size_t)r * n1 + j];
-        }
-        __syncthreads();
-        spectral_derivative<R>(sb, S, H1);
-        for (int k = threadIdx.x; k < n1; k += kThreads) {
-          const size_t p = (size_t)r * n1 + k;
-          for (int s = 0; s < S; ++s) {
-            C acc = sb[s * n1 + k];
-            for (int t = 0; t < S; ++t)
-              if (t != s) acc = caxpy_r(coupling2(F1, N, S, s, t, p), U[(size_t)t * N + p], acc);
-            const C xs = x[(size_t)s * N + p];
-            const R v = __ldg(V + (size_t)s * N + p);
-            T[(size_t)s * N + p] = cmk<C>(fma(mh, acc.x, v * xs.x), fma(mh, acc.y, v * xs.y));
-          }
-        }
-        __syncthreads();
+      }
+      __syncthreads();
       }
     }
     good = good && grid_barrier(I->bar, I->err);
-    // ---- dimension 0 (columns, stride n1): y = e z + a x + c (T - h2m_0 (D_0 + F_0)^2 x)
+    // ---- dimension 0 (columns, stride n1): y = e z + a x + c (T - h2m_0 (D_0 + F_0)^2 x).
+    // All owned columns and surfaces form one batch: vector (col_local * S + s).
     {
       const HOp<R>& H0 = H[0];
       const R mh = -(R)I->h2m[0];
       const R* F0 = F;
-      for (int col = c_lo; col < c_hi; ++col) {
-        for (int k = threadIdx.x; k < S * n0; k += kThreads) {
-          const int s = k / n0, i = k - s * n0;
-          sb[k] = x[(size_t)s * N + (size_t)i * n1 + col];
+      const int cb = max(1, min(c_hi - c_lo, cap_elems / (S * n0)));
+      for (int c0 = c_lo; c0 < c_hi; c0 += cb) {
+      const int ncol = min(cb, c_hi - c0);
+      const int nv = ncol * S;
+      for (int k = threadIdx.x; k < nv * n0; k += kThreads) {
+        const int v = k / n0, i = k - v * n0;
+        const int cl = v / S, s = v - cl * S;
+        sb[spad<C>(k)] = x[(size_t)s * N + (size_t)i * n1 + (c0 + cl)];
+      }
+      __syncthreads();
+      if (nv > 0) spectral_derivative<R>(sb, nv, H0);
+      for (int k = threadIdx.x; k < ncol * n0; k += kThreads) {
+        const int cl = k / n0, i = k - cl * n0;
+        const size_t p = (size_t)i * n1 + (c0 + cl);
+        for (int s = 0; s < S; ++s) {
+          const int e = (cl * S + s) * n0 + i;
+          C acc = sb[spad<C>(e)];
+          for (int t = 0; t < S; ++t)
+            if (t != s) acc = caxpy_r(coupling2(F0, N, S, s, t, p), x[(size_t)t * N + p], acc);
+          U[(size_t)s * N + p] = acc;
+          sb[spad<C>(e)] = acc;
         }
-        __syncthreads();
-        spectral_derivative<R>(sb, S, H0);
-        for (int i = threadIdx.x; i < n0; i += kThreads) {
-          const size_t p = (size_t)i * n1 + col;
-          for (int s = 0; s < S; ++s) {
-            C acc = sb[s * n0 + i];
-            for (int t = 0; t < S; ++t)
-              if (t != s) acc = caxpy_r(coupling2(F0, N, S, s, t, p), x[(size_t)t * N + p], acc);
-            U[(size_t)s * N + p] = acc;
-            sb[s * n0 + i] = acc;
-          }
+      }
+      __syncthreads();
+      if (nv > 0) spectral_derivative<R>(sb, nv, H0);
+      for (int k = threadIdx.x; k < ncol * n0; k += kThreads) {
+        const int cl = k / n0, i = k - cl * n0;
+        const size_t p = (size_t)i * n1 + (c0 + cl);
+        for (int s = 0; s < S; ++s) {
+          C acc = sb[spad<C>((cl * S + s) * n0 + i)];
+          for (int t = 0; t < S; ++t)
+            if (t != s) acc = caxpy_r(coupling2(F0, N, S, s, t, p), U[(size_t)t * N + p], acc);
+          const C tt = T[(size_t)s * N + p];
+          const C hx = cmk<C>(fma(mh, acc.x, tt.x), fma(mh, acc.y, tt.y));
+          const C xs = x[(size_t)s * N + p];
+          C out = caxpy(c, hx, cmk<C>(a * xs.x, a * xs.y));
+          if (e != (R)0) out = caxpy_r(e, z[(size_t)s * N + p], out);
+          y[(size_t)s * N + p] = out;
         }
-        __syncthreads();
-        spectral_derivative<R>(sb, S, H0);
-        for (int i = threadIdx.x; i < n0; i += kThreads) {
-          const size_t p = (size_t)i * n1 + col;
-          for (int s = 0; s < S; ++s) {
-            C acc = sb[s * n0 + i];
-            for (int t = 0; t < S; ++t)
-              if (t != s) acc = caxpy_r(coupling2(F0, N, S, s, t, p), U[(size_t)t * N + p], acc);
-            const C tt = T[(size_t)s * N + p];
-            const C hx = cmk<C>(fma(mh, acc.x, tt.x), fma(mh, acc.y, tt.y));
-            const C xs = x[(size_t)s * N + p];
-            C out = caxpy(c, hx, cmk<C>(a * xs.x, a * xs.y));
-            if (e != (R)0) out = caxpy_r(e, z[(size_t)s * N + p], out);
-            y[(size_t)s * N + p] = out;
-          }
-        }
-        __syncthreads();
+      }
+      __syncthreads();
       }
     }
     good = good && grid_barrier(I->bar, I->err);
@@ -278,6 +292,8 @@ __device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_bytes, 
   }
   D.parity = 0;
   D.good = true;
+  // padded_bytes(e, 16) = 16 (e + e/8 + 1) rounded up: invert conservatively
+  D.cap_elems = (int)(((size_t)fft_bytes / 16 - 2) * 8 / 9);
   return D;
 }
 
@@ -380,9 +396,20 @@ cudaError_t qg_selftest_barrier(int* d_words, int* h_timed_out, int* h_passed) {
   return e;
 }
 
+int qg_grid2d_ctas(const Inst2D& I);
+
+// One FFT batch holds every owned row (or column) of every surface.
 static size_t fft2d_bytes(const Inst2D& I) {
+  const int G = qg_grid2d_ctas(I);
+  const int rp = (I.n[0] + G - 1) / G, cp = (I.n[1] + G - 1) / G;
+  const size_t rows = (size_t)rp * I.n[1], cols = (size_t)cp * I.n[0];
   const int nmax = I.n[0] > I.n[1] ? I.n[0] : I.n[1];
-  return qg::align16(sizeof(double2) * (size_t)I.S * nmax);
+  size_t want = (size_t)I.S * (rows > cols ? rows : cols);
+  // at most 96 KB of batch; always room for one row or column of every surface
+  const size_t cap = (size_t)96 * 1024 / 18;
+  if (want > cap) want = cap;
+  if (want < (size_t)I.S * nmax) want = (size_t)I.S * nmax;
+  return qg::padded_bytes(want, sizeof(double2));
 }
 
 int qg_grid2d_ctas(const Inst2D& I) {
