@@ -494,6 +494,7 @@ def run_2d(args):
         st.set_gaussian(1, q0, p0, s0)
         for _ in range(args.warmup):
             st.propagate(1, 6, 1, dt, 1, opts)
+        tune = st.autotune(1, 6, 1, dt, 1, opts) if not args.no_autotune else None
         st.set_gaussian(1, q0, p0, s0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -502,7 +503,7 @@ def run_2d(args):
         s_ = st.propagate(1, 6, 1, dt, args.steps, opts)
         e1.record()
         torch.cuda.synchronize()
-        res[name] = dict(ms=e0.elapsed_time(e1), stats=s_, psi=st.get(), norm=st.norm())
+        res[name] = dict(ms=e0.elapsed_time(e1), stats=s_, psi=st.get(), norm=st.norm(), tune=tune)
     dv = np.prod([(p["qmax"][d] - p["qmin"][d]) / ns[d] for d in range(2)])
     err = float(np.linalg.norm(res["mixed"]["psi"] - res["fp64"]["psi"]) * np.sqrt(dv))
     t_m, t_f = res["mixed"]["ms"], res["fp64"]["ms"]
@@ -519,7 +520,9 @@ def run_2d(args):
             "mixed_vs_fp64_l2": err, "norm_drift": abs(res["mixed"]["norm"] - 1.0),
             "mixed_hpsi": {"fp64": res["mixed"]["stats"]["n_hpsi"], "c64": res["mixed"]["stats"]["n_hpsi32"]},
             "hpsi_grid_point_applications_per_s":
-                (res["mixed"]["stats"]["n_hpsi"] + res["mixed"]["stats"]["n_hpsi32"]) * ns[0] * ns[1] / (t_m / 1e3)}
+                (res["mixed"]["stats"]["n_hpsi"] + res["mixed"]["stats"]["n_hpsi32"]) * ns[0] * ns[1] / (t_m / 1e3),
+            # one-step trial times (ms) at the automatic cooperative width, 1/2 and 1/4 of it
+            "launch_width_trials_ms": {k: res[k]["tune"] for k in ("mixed", "fp64")}}
     print(json.dumps(line), flush=True)
 
 

@@ -107,8 +107,16 @@ typedef struct qg_batch* qg_batch_t;
  * solver: QG_SOLVER_GMRES (default; restarted GMRES with Arnoldi/CGS as in
  *      Sec. II B) or QG_SOLVER_LANCZOS (the same minimal-residual iterates by
  *      the three-term recurrence that the Hermitian H allows: 5 work vectors,
- *      O(1) vector passes per iteration; needs restart >= 4). */
+ *      O(1) vector passes per iteration; needs restart >= 4).
+ * guess: QG_GUESS_EULER (default) starts each implicit solve from the
+ *      explicit-Euler step (1 - i tau H) b, as in Sec. II B; QG_GUESS_ZERO
+ *      starts from zero, so the first residual is b and no H psi is spent on
+ *      the guess or its residual.  For a minimal-residual solver the zero
+ *      start after k + 2 iterations searches K_{k+2}(H, b), a space that
+ *      contains everything the Euler start reaches after k iterations at the
+ *      same H psi count; both stop at the same tolerance. */
 enum { QG_SOLVER_GMRES = 0, QG_SOLVER_LANCZOS = 1 };
+enum { QG_GUESS_EULER = 0, QG_GUESS_ZERO = 1 };
 typedef struct {
   double tol;
   int restart;
@@ -119,6 +127,7 @@ typedef struct {
   double inner_tol;
   int max_outer;
   int solver;
+  int guess;
 } qg_solver_opts;
 
 /* Statistics of one propagate / step call (summed over all sub-steps). */
@@ -180,6 +189,15 @@ void qg_destroy_state(qg_state_t s);
 /* Stream (cudaStream_t) on which the state's work is ordered; NULL = the
  * legacy default stream. */
 qg_status qg_state_set_stream(qg_state_t s, void* stream);
+/* 2-D grids: number of CTAs of the cooperative launch that carries the
+ * state (0 = automatic: the largest power of two not above the SM count and
+ * the shorter grid side).  qg_state_autotune times trial_steps composed steps
+ * at the automatic width and at 1/2 and 1/4 of it (restoring psi after each
+ * trial), keeps the fastest and writes the three trial times (ms) to ms_out
+ * (may be NULL).  No effect on 1-D states, which run on one CTA each. */
+qg_status qg_state_set_launch_width(qg_state_t s, int ctas);
+qg_status qg_state_autotune(qg_state_t s, int method, int order, int scheme, double dt, int64_t trial_steps,
+                            const qg_solver_opts* opts, double* ms_out);
 qg_status qg_set_state(qg_state_t s, const void* psi, int on_device);
 qg_status qg_get_state(qg_state_t s, void* psi, int on_device);
 /* Gaussian wavepacket on one surface, zero on the others (Sec. III):

@@ -31,6 +31,8 @@ QG_C128 = 0
 QG_C64_MIXED = 1
 QG_SOLVER_GMRES = 0
 QG_SOLVER_LANCZOS = 1
+QG_GUESS_EULER = 0
+QG_GUESS_ZERO = 1
 QG_RUN_FORWARD = 0
 QG_RUN_CHECKPOINT = 1
 QG_RUN_ADJOINT = 2
@@ -42,7 +44,8 @@ EXPORTED = [
     "qg_destroy_state", "qg_state_set_stream", "qg_set_state", "qg_get_state", "qg_set_gaussian",
     "qg_apply_h", "qg_step_implicit", "qg_propagate", "qg_norm", "qg_energy", "qg_population",
     "qg_overlap", "qg_batch_propagate", "qg_batch_create", "qg_batch_run", "qg_batch_capture", "qg_batch_replay", "qg_batch_stats",
-    "qg_batch_stream", "qg_batch_destroy", "qg_batch_autotune", "qg_batch_tuning", "qg_selftest_barrier_timeout", "qg_state_set_adjoint", "qg_propagate_ex", "qg_batch_run_ex", "qg_propagate_noalloc", "qg_status_string", "qg_last_error_string", "qg_version",
+    "qg_batch_stream", "qg_batch_destroy", "qg_batch_autotune", "qg_batch_tuning", "qg_selftest_barrier_timeout", "qg_state_set_launch_width",
+    "qg_state_autotune", "qg_state_set_adjoint", "qg_propagate_ex", "qg_batch_run_ex", "qg_propagate_noalloc", "qg_status_string", "qg_last_error_string", "qg_version",
 ]
 
 
@@ -59,7 +62,8 @@ class QgError(RuntimeError):
 class SolverOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("reorth", ctypes.c_int), ("midpoint_epilogue", ctypes.c_int), ("true_residual", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("solver", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("solver", ctypes.c_int),
+                ("guess", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -120,6 +124,9 @@ def lib():
                                       ctypes.POINTER(ctypes.c_double)]),
             "qg_batch_tuning": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
             "qg_selftest_barrier_timeout": (I, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+            "qg_state_set_launch_width": (I, [P, I]),
+            "qg_state_autotune": (I, [P, I, I, I, D, ctypes.c_int64, ctypes.POINTER(SolverOpts),
+                                      ctypes.POINTER(ctypes.c_double)]),
             "qg_batch_destroy": (V, [P]),
             "qg_state_set_adjoint": (I, [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P]),
             "qg_propagate_ex": (I, [P, I, I, I, I, D, ctypes.c_int64, ctypes.POINTER(SolverOpts),
@@ -309,6 +316,15 @@ class State:
         r = lib().qg_step_implicit(self.handle, method, order, scheme, float(dt), ctypes.byref(o), ctypes.byref(st))
         _check(r, "qg_step_implicit", allow=(QG_ERR_NOT_CONVERGED,) if allow_fail else ())
         return st.as_dict()
+
+    def autotune(self, method, order, scheme, dt, trial_steps=1, opts=None):
+        """2-D states: pick the fastest cooperative launch width; returns the
+        trial times (ms) at the automatic width, 1/2 and 1/4 of it."""
+        o = opts if opts is not None else default_solver_opts()
+        ms = (ctypes.c_double * 3)()
+        _check(lib().qg_state_autotune(self.handle, method, order, scheme, float(dt), int(trial_steps),
+                                       ctypes.byref(o), ms), "qg_state_autotune")
+        return list(ms)
 
     def norm(self):
         v = ctypes.c_double()

@@ -11,10 +11,20 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libqgeom.so")
-SOURCES = ["qg_api.cu", "qg_kernels.cu", "qg_kernels2d.cu"]
-# 2-D kernels: CTAs read data other CTAs wrote in the same launch, so global
-# loads are cached in L2 only
-EXTRA = {"qg_kernels2d.cu": ["-Xptxas", "-dlcm=cg"]}
+# (source, object, extra flags): the persistent 1-D propagator is compiled once
+# per occupancy and the 2-D one once per precision form, so the large
+# instantiations build in parallel.  In the 2-D kernels CTAs read data other
+# CTAs wrote in the same launch, so their global loads are cached in L2 only.
+UNITS = [
+    ("qg_propagate.cu", "qg_propagate_b1.o", ["-DQG_MINB=1"]),
+    ("qg_propagate.cu", "qg_propagate_b2.o", ["-DQG_MINB=2"]),
+    ("qg_propagate2d.cu", "qg_propagate2d_f64.o", ["-DQG_PREC=0", "-Xptxas", "-dlcm=cg"]),
+    ("qg_propagate2d.cu", "qg_propagate2d_mixed.o", ["-DQG_PREC=1", "-Xptxas", "-dlcm=cg"]),
+    ("qg_kernels2d.cu", "qg_kernels2d.o", ["-Xptxas", "-dlcm=cg"]),
+    ("qg_noalloc.cu", "qg_noalloc.o", []),
+    ("qg_kernels.cu", "qg_kernels.o", []),
+    ("qg_api.cu", "qg_api.o", []),
+]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -38,9 +48,10 @@ def build(force=False, verbose=False):
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc] + ARCH + FLAGS + EXTRA.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, obj, extra = unit
+        obj = os.path.join(BUILD, obj)
+        cmd = [nvcc] + ARCH + FLAGS + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))
@@ -48,8 +59,8 @@ def build(force=False, verbose=False):
             print(r.stderr, file=sys.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with cf.ThreadPoolExecutor(len(UNITS)) as ex:
+        objs = list(ex.map(compile_one, UNITS))
     tmp = LIB + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)

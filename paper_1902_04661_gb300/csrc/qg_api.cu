@@ -119,6 +119,7 @@ void default_opts(qg_solver_opts* o) {
   o->inner_tol = 1e-6;
   o->max_outer = 10;
   o->solver = QG_SOLVER_GMRES;
+  o->guess = QG_GUESS_EULER;
 }
 
 bool valid_opts(const qg_solver_opts& o) {
@@ -126,7 +127,8 @@ bool valid_opts(const qg_solver_opts& o) {
          (o.reorth == 0 || o.reorth == 1) && (o.midpoint_epilogue == 0 || o.midpoint_epilogue == 1) &&
          (o.true_residual == 0 || o.true_residual == 1) && o.inner_tol > 0.0 && o.inner_tol < 1.0 &&
          o.max_outer >= 1 && o.max_outer <= 1000 &&
-         (o.solver == QG_SOLVER_GMRES || (o.solver == QG_SOLVER_LANCZOS && o.restart >= 4));
+         (o.solver == QG_SOLVER_GMRES || (o.solver == QG_SOLVER_LANCZOS && o.restart >= 4)) &&
+         (o.guess == QG_GUESS_EULER || o.guess == QG_GUESS_ZERO);
 }
 
 // Composition fractions (Sec. II C): order 2 is the elementary step; each
@@ -219,6 +221,7 @@ Inst2D make_inst2d(const qg_state* s) {
   I.ckpt = s->adj.ckpt;
   I.nckpt = s->adj.nckpt;
   I.every = s->adj.every > 0 ? s->adj.every : 1;
+  I.ctas = s->launch_ctas;
   return I;
 }
 
@@ -229,6 +232,11 @@ double grid_dv(const qg_grid* g) {
 }
 
 }  // namespace
+
+extern "C" {
+static qg_status build_plan(int method, int order, int scheme, double dt, int64_t nsteps, const qg_solver_opts* opts,
+                            StepPlan* P);
+}
 
 static qg_status upload_desc(qg_state_t s) {
   InstDesc d = make_desc(s);
@@ -503,6 +511,60 @@ void qg_destroy_state(qg_state_t s) {
   delete s;
 }
 
+qg_status qg_state_set_launch_width(qg_state_t s, int ctas) {
+  if (!s || ctas < 0) return QG_ERR_INVALID_ARG;
+  s->launch_ctas = ctas;
+  return QG_OK;
+}
+
+qg_status qg_state_autotune(qg_state_t s, int method, int order, int scheme, double dt, int64_t trial_steps,
+                            const qg_solver_opts* opts, double* ms_out) {
+  if (!s || trial_steps < 1) return QG_ERR_INVALID_ARG;
+  if (s->m->g->D != 2) return QG_OK;   // 1-D states run on one CTA: nothing to tune
+  StepPlan P;
+  qg_status st = build_plan(method, order, scheme, dt, trial_steps, opts, &P);
+  if (st != QG_OK) return st;
+  if (P.restart > QG_MAX_RESTART - 1) return QG_ERR_UNSUPPORTED;
+  const size_t len = (size_t)s->m->S * s->m->g->ntot;
+  double2* save = nullptr;
+  QG_TRY(cudaMalloc(&save, sizeof(double2) * len));
+  s->launch_ctas = 0;
+  const int gmax = qg_grid2d_ctas(make_inst2d(s));
+  const int cand[3] = {gmax, gmax / 2 > 0 ? gmax / 2 : 1, gmax / 4 > 0 ? gmax / 4 : 1};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(save, s->d_psi, sizeof(double2) * len, cudaMemcpyDeviceToDevice, s->stream);
+  double best = 1e300;
+  int bi = 0;
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+    s->launch_ctas = cand[c];
+    e = cudaEventRecord(e0, s->stream);
+    if (e == cudaSuccess) e = qg_launch_propagate2d(make_inst2d(s), P, s->d_stats, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = -1.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    if (ms_out) ms_out[c] = ms;
+    if (ms > 0.f && ms < best) {
+      best = ms;
+      bi = c;
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->d_psi, save, sizeof(double2) * len, cudaMemcpyDeviceToDevice, s->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(save);
+  if (e != cudaSuccess) {
+    set_err("qg_state_autotune", e);
+    return QG_ERR_CUDA;
+  }
+  s->launch_ctas = cand[bi];
+  return QG_OK;
+}
+
 qg_status qg_state_set_stream(qg_state_t s, void* stream) {
   if (!s) return QG_ERR_INVALID_ARG;
   s->stream = (cudaStream_t)stream;
@@ -584,6 +646,7 @@ static qg_status build_plan(int method, int order, int scheme, double dt, int64_
   P->inner_tol = o.inner_tol;
   P->max_outer = o.max_outer;
   P->solver = o.solver;
+  P->guess = o.guess;
   return QG_OK;
 }
 
@@ -1023,6 +1086,7 @@ qg_status qg_propagate_noalloc(int N, double qmin, double qmax, int S, double ma
   P.inner_tol = o.inner_tol;
   P.max_outer = o.max_outer;
   P.solver = o.solver;
+  P.guess = o.guess;
   const FftPlan plan = make_plan(N);
   qg_step_stats h;
   memset(&h, 0, sizeof(h));

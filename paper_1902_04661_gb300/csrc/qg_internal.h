@@ -77,6 +77,7 @@ struct qg_state {
   double* d_scalars;        // small device scratch for observables
   qg_state_adjoint adj;     // caller-owned adjoint buffers (or nulls)
   unsigned char* d_coop;    // 2-D grids: barrier words, error flag, partial sums
+  int launch_ctas;          // 2-D grids: cooperative launch width (0 = automatic)
 };
 
 // Everything one CTA needs to work on one instance (a state with its model
@@ -136,6 +137,7 @@ struct Inst2D {
   double2* ckpt;
   long long nckpt;
   long long every;
+  int ctas;            // cooperative launch width (0 = automatic)
 };
 
 // Parameters of one propagate launch (passed by value).
@@ -154,6 +156,7 @@ struct StepPlan {
   int max_outer;
   int run;   // QG_RUN_FORWARD, QG_RUN_CHECKPOINT or QG_RUN_ADJOINT
   int solver;  // QG_SOLVER_GMRES or QG_SOLVER_LANCZOS
+  int guess;   // QG_GUESS_EULER or QG_GUESS_ZERO
   double frac[QG_MAX_FRACTIONS];
 };
 
@@ -177,6 +180,18 @@ struct qg_batch {
 size_t qg_smem_bytes(int max_n, int max_S, int restart);
 cudaError_t qg_launch_propagate(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
                                 qg_step_stats* d_stats, int max_n, int max_S, cudaStream_t st);
+// The persistent propagator built for MINB CTAs per SM (one translation unit
+// each); grid 0 only sets the kernel's shared-memory attribute.
+template <int MINB>
+cudaError_t qg_launch_propagate_minb(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
+                                     qg_step_stats* d_stats, int max_n, int nb, size_t smem, int grid,
+                                     cudaStream_t st);
+template <>
+cudaError_t qg_launch_propagate_minb<1>(const InstDesc*, int, const StepPlan&, int*, qg_step_stats*, int, int, size_t,
+                                        int, cudaStream_t);
+template <>
+cudaError_t qg_launch_propagate_minb<2>(const InstDesc*, int, const StepPlan&, int*, qg_step_stats*, int, int, size_t,
+                                        int, cudaStream_t);
 cudaError_t qg_launch_propagate_tuned(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
                                       qg_step_stats* d_stats, int max_n, int max_S, int ctas_per_sm, int nb_pref,
                                       cudaStream_t st);
@@ -190,7 +205,16 @@ cudaError_t qg_launch_gaussian(double2* d_psi, int n, int S, int surface, double
 cudaError_t qg_noalloc_launch(int n, double qmin, double qmax, int S, double mass, const double* V, const double* F,
                               double2* psi, const FftPlan& plan, const StepPlan& P, qg_step_stats* host_stats,
                               cudaStream_t st);
+// Host stub of the 2-D propagator kernel for one precision form (0:
+// complex128, 1: mixed), one translation unit each.
+template <int PREC>
+const void* qg_propagate2d_fn();
+template <>
+const void* qg_propagate2d_fn<0>();
+template <>
+const void* qg_propagate2d_fn<1>();
 cudaError_t qg_launch_propagate2d(const Inst2D& I, const StepPlan& P, qg_step_stats* d_stats, cudaStream_t st);
+int qg_grid2d_ctas(const Inst2D& I);
 cudaError_t qg_launch_apply_h2d(const Inst2D& I, double2* d_out, double* d_energy, cudaStream_t st);
 cudaError_t qg_launch_gaussian2d(double2* d_psi, const int* n, int S, int surface, const double* qmin,
                                  const double* dq, const double* q0, const double* p0, const double* s0,

@@ -1,318 +1,12 @@
-// Two-dimensional grids: one instance is spread over every CTA of one
-// cooperative launch (all CTAs co-resident).  Each CTA owns a band of rows
-// (q1 index) for the pointwise work and the dimension-1 transforms, and a
-// band of columns for the dimension-0 transforms; a bounded grid barrier
-// separates the phases.  Sums over the state are formed per CTA, exchanged
-// through global memory and added by every CTA in the same fixed order, so
-// every CTA takes the same decisions.
-//
-// This file is compiled with -Xptxas -dlcm=cg: global loads are cached in L2
-// only, so data written by other CTAs in the same launch is never read from a
-// stale L1 line.
+// Two-dimensional grids: the Hamiltonian action and energy, the Gaussian
+// initial state, the grid-barrier self-test and the host launch wrappers (the
+// propagator kernels are in their own translation units).  Compiled with
+// -Xptxas -dlcm=cg like every unit that uses the 2-D domain.
 #include <cuda_runtime.h>
 
-#include "qg_solver.cuh"
+#include "qg_dom2d.cuh"
 
 namespace qg {
-
-// Bounded sense-reversing grid barrier (all CTAs are co-resident under the
-// cooperative launch).  A CTA that waits more than about a second gives up,
-// raises the error flag and returns false; every later barrier then fails
-// too, so every CTA leaves the kernel.
-__device__ bool grid_barrier(unsigned* bar, int* err) {
-  __shared__ int s_fail;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-    int fail = 0;
-    if (arrived == gridDim.x) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*gen == g) {
-        if (++spins > (1LL << 24)) {
-          fail = 1;
-          atomicExch(err, 1);
-          break;
-        }
-        if (*(volatile int*)err) {   // another CTA already gave up
-          fail = 1;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    if (*(volatile int*)err) fail = 1;
-    s_fail = fail;
-  }
-  __syncthreads();
-  return s_fail == 0;
-}
-
-struct Dom2D {
-  const Inst2D* I;
-  int len, N, n0, n1, S;
-  int r_lo, r_hi, c_lo, c_hi;
-  double dv;
-  unsigned char* gm;
-  double* red;
-  unsigned char* fb;
-  HOp<double> H64[2];
-  HOp<float> H32[2];
-  double2 *U64, *T64;
-  float2 *U32, *T32;
-  double2* basis64;
-  double2* res64;
-  float2 *r32, *d32, *basis32;
-  int parity;
-  bool good;
-  int cap_elems;   // complex values one shared-memory FFT batch may hold
-
-  template <class F>
-  __device__ __forceinline__ void each(F&& f) {
-    const int rows = r_hi - r_lo;
-    const int per = rows * n1;
-    const int tot = S * per;
-    for (int k = threadIdx.x; k < tot; k += kThreads) {
-      const int s = k / per;
-      f(s * N + r_lo * n1 + (k - s * per));
-    }
-  }
-
-  template <int K, typename R>
-  __device__ __forceinline__ bool sum(R (&v)[K], R* out) {
-    cta_sum<K>(v, reinterpret_cast<R*>(red), out);
-    R* buf = reinterpret_cast<R*>(I->gred + (size_t)parity * gridDim.x * 32);
-    parity ^= 1;
-    if (threadIdx.x < K) buf[blockIdx.x * 32 + threadIdx.x] = out[threadIdx.x];
-    good = good && grid_barrier(I->bar, I->err);
-    if (threadIdx.x < K) {
-      R s = 0;
-      for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(buf + b * 32 + threadIdx.x);
-      out[threadIdx.x] = s;
-    }
-    __syncthreads();
-    return good;
-  }
-
-  __device__ __forceinline__ bool ok() const { return good; }
-
-  // y = e z + a x + c (H x), H = sum_d -hbar^2/2m_d (D_d + F_d)^2 + V.
-  template <typename R>
-  __device__ void hpsi(const typename Cx<R>::T* x, typename Cx<R>::T* y, const typename Cx<R>::T* z, R e, R a,
-                       typename Cx<R>::T c) {
-    using C = typename Cx<R>::T;
-    C* sb = reinterpret_cast<C*>(fb);
-    const HOp<R>* H = nullptr;
-    C* U;
-    C* T;
-    const R* V;
-    const R* F;
-    if constexpr (sizeof(R) == 8) {
-      H = H64;
-      U = U64;
-      T = T64;
-      V = I->V;
-      F = I->F;
-    } else {
-      H = H32;
-      U = U32;
-      T = T32;
-      V = I->V32;
-      F = I->F32;
-    }
-    const int npair = S * (S - 1) / 2;
-    // ---- dimension 1 (rows, contiguous): T = -h2m_1 (D_1 + F_1)^2 x + V x.
-    // All owned rows and all surfaces form one shared-memory FFT batch:
-    // vector (row_local * S + s) holds x_s on that row.
-    {
-      const HOp<R>& H1 = H[1];
-      const R mh = -(R)I->h2m[1];
-      const R* F1 = F + (size_t)1 * npair * N;
-      const int rb = max(1, min(r_hi - r_lo, cap_elems / (S * n1)));
-      for (int r0 = r_lo; r0 < r_hi; r0 += rb) {
-      const int nrow = min(rb, r_hi - r0);
-      const int nv = nrow * S;
-      for (int k = threadIdx.x; k < nv * n1; k += kThreads) {
-        const int v = k / n1, j = k - v * n1;
-        const int rl = v / S, s = v - rl * S;
-        sb[spad<C>(k)] = x[(size_t)s * N + (size_t)(r0 + rl) * n1 + j];
-      }
-      __syncthreads();
-      if (nv > 0) spectral_derivative<R>(sb, nv, H1);
-      for (int k = threadIdx.x; k < nrow * n1; k += kThreads) {
-        const int rl = k / n1, j = k - rl * n1;
-        const size_t p = (size_t)(r0 + rl) * n1 + j;
-        for (int s = 0; s < S; ++s) {
-          const int e = (rl * S + s) * n1 + j;
-          C acc = sb[spad<C>(e)];
-          for (int t = 0; t < S; ++t)
-            if (t != s) acc = caxpy_r(coupling2(F1, N, S, s, t, p), x[(size_t)t * N + p], acc);
-          U[(size_t)s * N + p] = acc;
-          sb[spad<C>(e)] = acc;
-        }
-      }
-      __syncthreads();
-      if (nv > 0) spectral_derivative<R>(sb, nv, H1);
-      for (int k = threadIdx.x; k < nrow * n1; k += kThreads) {
-        const int rl = k / n1, j = k - rl * n1;
-        const size_t p = (size_t)(r0 + rl) * n1 + j;
-        for (int s = 0; s < S; ++s) {
-          C acc = sb[spad<C>((rl * S + s) * n1 + j)];
-          for (int t = 0; t < S; ++t)
-            if (t != s) acc = caxpy_r(coupling2(F1, N, S, s, t, p), U[(size_t)t * N + p], acc);
-          const C xs = x[(size_t)s * N + p];
-          const R v = __ldg(V + (size_t)s * N + p);
-          T[(size_t)s * N + p] = cmk<C>(fma(mh, acc.x, v * xs.x), fma(mh, acc.y, v * xs.y));
-        }
-      }
-      __syncthreads();
-      }
-    }
-    good = good && grid_barrier(I->bar, I->err);
-    // ---- dimension 0 (columns, stride n1): y = e z + a x + c (T - h2m_0 (D_0 + F_0)^2 x).
-    // All owned columns and surfaces form one batch: vector (col_local * S + s).
-    {
-      const HOp<R>& H0 = H[0];
-      const R mh = -(R)I->h2m[0];
-      const R* F0 = F;
-      const int cb = max(1, min(c_hi - c_lo, cap_elems / (S * n0)));
-      for (int c0 = c_lo; c0 < c_hi; c0 += cb) {
-      const int ncol = min(cb, c_hi - c0);
-      const int nv = ncol * S;
-      for (int k = threadIdx.x; k < nv * n0; k += kThreads) {
-        const int v = k / n0, i = k - v * n0;
-        const int cl = v / S, s = v - cl * S;
-        sb[spad<C>(k)] = x[(size_t)s * N + (size_t)i * n1 + (c0 + cl)];
-      }
-      __syncthreads();
-      if (nv > 0) spectral_derivative<R>(sb, nv, H0);
-      for (int k = threadIdx.x; k < ncol * n0; k += kThreads) {
-        const int cl = k / n0, i = k - cl * n0;
-        const size_t p = (size_t)i * n1 + (c0 + cl);
-        for (int s = 0; s < S; ++s) {
-          const int e = (cl * S + s) * n0 + i;
-          C acc = sb[spad<C>(e)];
-          for (int t = 0; t < S; ++t)
-            if (t != s) acc = caxpy_r(coupling2(F0, N, S, s, t, p), x[(size_t)t * N + p], acc);
-          U[(size_t)s * N + p] = acc;
-          sb[spad<C>(e)] = acc;
-        }
-      }
-      __syncthreads();
-      if (nv > 0) spectral_derivative<R>(sb, nv, H0);
-      for (int k = threadIdx.x; k < ncol * n0; k += kThreads) {
-        const int cl = k / n0, i = k - cl * n0;
-        const size_t p = (size_t)i * n1 + (c0 + cl);
-        for (int s = 0; s < S; ++s) {
-          C acc = sb[spad<C>((cl * S + s) * n0 + i)];
-          for (int t = 0; t < S; ++t)
-            if (t != s) acc = caxpy_r(coupling2(F0, N, S, s, t, p), U[(size_t)t * N + p], acc);
-          const C tt = T[(size_t)s * N + p];
-          const C hx = cmk<C>(fma(mh, acc.x, tt.x), fma(mh, acc.y, tt.y));
-          const C xs = x[(size_t)s * N + p];
-          C out = caxpy(c, hx, cmk<C>(a * xs.x, a * xs.y));
-          if (e != (R)0) out = caxpy_r(e, z[(size_t)s * N + p], out);
-          y[(size_t)s * N + p] = out;
-        }
-      }
-      __syncthreads();
-      }
-    }
-    good = good && grid_barrier(I->bar, I->err);
-  }
-
-  // F_{st} at flattened point p from one dimension's upper triangle.
-  template <typename R>
-  __device__ static __forceinline__ R coupling2(const R* Fd, int N, int S, int s, int t, size_t p) {
-    if (s < t) {
-      const int q = s * S - (s * (s + 1)) / 2 + (t - s - 1);
-      return __ldg(Fd + (size_t)q * N + p);
-    }
-    const int q = t * S - (t * (t + 1)) / 2 + (s - t - 1);
-    return -__ldg(Fd + (size_t)q * N + p);
-  }
-};
-
-__device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_bytes, double* red) {
-  Dom2D D;
-  D.I = &I;
-  D.n0 = I.n[0];
-  D.n1 = I.n[1];
-  D.S = I.S;
-  D.N = D.n0 * D.n1;
-  D.len = D.S * D.N;
-  const int G = gridDim.x;
-  const int rp = (D.n0 + G - 1) / G, cp = (D.n1 + G - 1) / G;
-  D.r_lo = min(D.n0, (int)blockIdx.x * rp);
-  D.r_hi = min(D.n0, D.r_lo + rp);
-  D.c_lo = min(D.n1, (int)blockIdx.x * cp);
-  D.c_hi = min(D.n1, D.c_lo + cp);
-  D.dv = I.dv;
-  D.fb = dyn;
-  D.gm = dyn + fft_bytes;
-  D.red = red;
-  for (int d = 0; d < 2; ++d) {
-    D.H64[d].n = I.n[d];
-    D.H64[d].S = I.S;
-    D.H64[d].npass = I.npass[d];
-    for (int i = 0; i < QG_MAX_PASSES; ++i) D.H64[d].radix[i] = I.radix[d][i];
-    D.H64[d].h2m = I.h2m[d];
-    D.H64[d].tw = I.tw[d];
-    D.H64[d].kd = I.kd[d];
-    D.H32[d].n = I.n[d];
-    D.H32[d].S = I.S;
-    D.H32[d].npass = I.npass[d];
-    for (int i = 0; i < QG_MAX_PASSES; ++i) D.H32[d].radix[i] = I.radix[d][i];
-    D.H32[d].h2m = (float)I.h2m[d];
-    D.H32[d].tw = I.tw32[d];
-    D.H32[d].kd = I.kd32[d];
-  }
-  const size_t len = D.len;
-  // FP64 workspace: U, T, B, X, P0, basis (m + 1); the mixed form keeps its
-  // FP64 residual in basis slot 0.
-  D.U64 = I.work;
-  D.T64 = I.work + len;
-  D.basis64 = I.work + 5 * len;
-  D.res64 = D.basis64;
-  if (I.work32) {
-    D.U32 = I.work32;
-    D.T32 = I.work32 + len;
-    D.r32 = I.work32 + 2 * len;
-    D.d32 = I.work32 + 3 * len;
-    D.basis32 = I.work32 + 4 * len;
-  } else {
-    D.U32 = D.T32 = D.r32 = D.d32 = D.basis32 = nullptr;
-  }
-  D.parity = 0;
-  D.good = true;
-  // padded_bytes(e, 16) = 16 (e + e/8 + 1) rounded up: invert conservatively
-  D.cap_elems = (int)(((size_t)fft_bytes / 16 - 2) * 8 / 9);
-  return D;
-}
-
-__global__ void __launch_bounds__(QG_THREADS, 1) propagate2d_kernel(const Inst2D I, const StepPlan P, int fft_bytes,
-                                                                    qg_step_stats* st) {
-  extern __shared__ __align__(16) unsigned char dyn[];
-  __shared__ double red[kWarps * 16];
-  __shared__ double sc[64];
-  Dom2D D = make_dom2d(I, dyn, fft_bytes, red);
-  const size_t len = D.len;
-  Counters cnt{0, 0, 0, 0, 0, 0, 0, 0, 0.0};
-  long long nsub = 0;
-  const long long failed = run_steps(D, P, I.psi, I.work + 2 * len, I.work + 3 * len, I.work + 4 * len,
-                                     I.precision == QG_C64_MIXED, I.ckpt, I.nckpt, I.every, cnt, nsub, sc);
-  if (blockIdx.x == 0) {
-    write_stats(st, cnt, nsub, failed);
-    if (threadIdx.x == 0 && !D.good) st->status = QG_ERR_TIMEOUT;
-  }
-}
 
 // out = H psi (c = 1) or <psi|H|psi> (energy != null).
 __global__ void __launch_bounds__(QG_THREADS, 1) apply_h2d_kernel(const Inst2D I, int fft_bytes, double2* out,
@@ -419,6 +113,7 @@ int qg_grid2d_ctas(const Inst2D& I) {
   int lim = I.n[0] < I.n[1] ? I.n[0] : I.n[1];
   int G = 1;
   while (G * 2 <= sms && G * 2 <= lim) G *= 2;
+  if (I.ctas > 0 && I.ctas < G) G = I.ctas;
   return G;
 }
 
@@ -446,7 +141,8 @@ cudaError_t qg_launch_propagate2d(const Inst2D& I, const StepPlan& P, qg_step_st
   Inst2D Ic = I;
   StepPlan Pc = P;
   void* args[] = {&Ic, &Pc, &fft, &d_stats};
-  return coop_launch((const void*)qg::propagate2d_kernel, G, smem, args, st);
+  const void* fn = I.precision == QG_C64_MIXED ? qg_propagate2d_fn<1>() : qg_propagate2d_fn<0>();
+  return coop_launch(fn, G, smem, args, st);
 }
 
 cudaError_t qg_launch_apply_h2d(const Inst2D& I, double2* d_out, double* d_energy, cudaStream_t st) {

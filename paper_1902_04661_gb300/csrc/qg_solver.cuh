@@ -74,6 +74,7 @@ struct SolveParams {
   int reorth;
   int true_res;
   int solver;   // QG_SOLVER_GMRES or QG_SOLVER_LANCZOS
+  int x0_zero;  // the initial guess is zero: the first residual is b itself
 };
 
 template <typename R, class Dom>
@@ -113,9 +114,14 @@ __device__ bool gmres_solve(Dom& D, const SolveParams& P, R tau, const typename 
   const R bn = sqrt(dv * sc[0]);
   const R target = (R)P.tol * bn;
   int total = 0;
-  // r0 = b - A X
-  D.template hpsi<R>(X, basis, b, (R)1, (R)-1, mic);
-  count_hpsi<R>(cnt);
+  // r0 = b - A X  (= b when X starts at zero)
+  if (P.x0_zero) {
+    D.each([&](int i) { basis[i] = b[i]; });
+    __syncthreads();
+  } else {
+    D.template hpsi<R>(X, basis, b, (R)1, (R)-1, mic);
+    count_hpsi<R>(cnt);
+  }
   for (int guard = 0; guard < P.max_iters + 2; ++guard) {
     C* V0 = basis;
     R bv[1] = {0};
@@ -324,9 +330,14 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
   const R target = (R)P.tol * bn;
   int total = 0;
   for (int guard = 0; guard < P.max_iters + 2; ++guard) {
-    // r = b - A X
-    D.template hpsi<R>(X, Vc, b, (R)1, (R)-1, mic);
-    count_hpsi<R>(cnt);
+    // r = b - A X  (= b on the first pass when X starts at zero)
+    if (guard == 0 && P.x0_zero) {
+      D.each([&](int i) { Vc[i] = b[i]; });
+      __syncthreads();
+    } else {
+      D.template hpsi<R>(X, Vc, b, (R)1, (R)-1, mic);
+      count_hpsi<R>(cnt);
+    }
     if (guard > 0) cnt.restart++;
     R rv[1] = {0};
     D.each([&](int i) {
@@ -476,8 +487,8 @@ __device__ __forceinline__ void dcopy(Dom& D, C* dst, const C* src) {
 // FP64 implicit solve (1 + i tau H) X = b with GMRES in FP64.
 template <class Dom>
 __device__ bool solve_fp64(Dom& D, const StepPlan& P, double tau, const double2* b, double2* X, Counters& cnt,
-                           double* sc) {
-  SolveParams sp{P.tol, P.restart, P.max_iters, P.reorth, P.true_res, P.solver};
+                           double* sc, int x0_zero = 0) {
+  SolveParams sp{P.tol, P.restart, P.max_iters, P.reorth, P.true_res, P.solver, x0_zero};
   double res = 0.0;
   const bool ok = P.solver == QG_SOLVER_LANCZOS ? lanczos_solve<double>(D, sp, tau, b, X, D.basis64, cnt, sc, &res)
                                                 : gmres_solve<double>(D, sp, tau, b, X, D.basis64, cnt, sc, &res);
@@ -491,7 +502,7 @@ __device__ bool solve_fp64(Dom& D, const StepPlan& P, double tau, const double2*
 // until ||r|| <= tol ||b||.
 template <class Dom>
 __device__ bool solve_mixed(Dom& D, const StepPlan& P, double tau, const double2* b, double2* X, Counters& cnt,
-                            double* sc) {
+                            double* sc, int x0_zero = 0) {
   double2* Rv = D.res64;
   float2* r32 = D.r32;
   float2* d32 = D.d32;
@@ -506,10 +517,15 @@ __device__ bool solve_mixed(Dom& D, const StepPlan& P, double tau, const double2
   if (!D.template sum<1>(nv, sc)) return false;
   const double bn = sqrt(dv * sc[0]);
   const double target = P.tol * bn;
-  SolveParams sp{P.inner_tol, P.restart, P.max_iters, P.reorth, 0, P.solver};
+  SolveParams sp{P.inner_tol, P.restart, P.max_iters, P.reorth, 0, P.solver, 1};
   for (int outer = 0; outer <= P.max_outer; ++outer) {
-    D.template hpsi<double>(X, Rv, b, 1.0, -1.0, mic);
-    cnt.hpsi++;
+    if (outer == 0 && x0_zero) {
+      D.each([&](int i) { Rv[i] = b[i]; });
+      __syncthreads();
+    } else {
+      D.template hpsi<double>(X, Rv, b, 1.0, -1.0, mic);
+      cnt.hpsi++;
+    }
     double rv[1] = {0.0};
     D.each([&](int i) {
       const double2 a = Rv[i];
@@ -589,7 +605,38 @@ __device__ __forceinline__ void write_stats(qg_step_stats* st, const Counters& c
 // state, B/X/P0 workspace vectors, ckpt optional checkpoints (every `every`
 // composed steps, nckpt of them).  Returns the index of the failed composed
 // step or -1.
-template <class Dom>
+// Solves (1 + i tau H) X = b: in FP64 (MODE 0), in the mixed-precision form
+// (MODE 1), or as `mixed` says at run time (MODE 2).  A kernel built for one
+// form compiles only that form.  X starts from the explicit-Euler guess
+// (1 - i tau H) b (Sec. II B) or, with QG_GUESS_ZERO, from zero: the
+// minimal-residual iterate from zero after k + 2 iterations minimises over
+// K_{k+2}(H, b), which contains every point the Euler guess reaches after k
+// iterations for the same k + 2 H psi evaluations.
+template <int MODE, class Dom>
+__device__ __forceinline__ bool implicit_solve(Dom& D, const StepPlan& P, double tau, const double2* b, double2* X,
+                                               bool mixed, Counters& cnt, double* sc) {
+  const int zero = P.guess == QG_GUESS_ZERO;
+  if (zero) {
+    D.each([&](int i) { X[i] = make_double2(0.0, 0.0); });
+    __syncthreads();
+  }
+  if constexpr (MODE != 0) {
+    if (MODE == 1 || mixed) {
+      if (!zero) guess_mixed(D, tau, b, X, cnt);
+      return solve_mixed(D, P, tau, b, X, cnt, sc, zero);
+    }
+  }
+  if constexpr (MODE != 1) {
+    if (!zero) {
+      D.template hpsi<double>(b, X, nullptr, 0.0, 1.0, make_double2(0.0, -tau));
+      cnt.hpsi += 1;
+    }
+    return solve_fp64(D, P, tau, b, X, cnt, sc, zero);
+  }
+  return false;
+}
+
+template <int MODE, class Dom>
 __device__ long long run_steps(Dom& D, const StepPlan& P, double2* psi, double2* B, double2* X, double2* P0,
                                bool mixed, double2* ckpt, long long nckpt, long long every, Counters& cnt,
                                long long& nsub, double* sc) {
@@ -607,26 +654,12 @@ __device__ long long run_steps(Dom& D, const StepPlan& P, double2* psi, double2*
         // b = (1 - i tau H) psi ; guess x0 = (1 - i tau H) b ; solve (1 + i tau H) x = b
         D.template hpsi<double>(psi, B, nullptr, 0.0, 1.0, mic);
         cnt.hpsi += 1;
-        if (mixed) {
-          guess_mixed(D, tau, B, X, cnt);
-          ok = solve_mixed(D, P, tau, B, X, cnt, sc);
-        } else {
-          D.template hpsi<double>(B, X, nullptr, 0.0, 1.0, mic);
-          cnt.hpsi += 1;
-          ok = solve_fp64(D, P, tau, B, X, cnt, sc);
-        }
+        ok = implicit_solve<MODE>(D, P, tau, B, X, mixed, cnt, sc);
         if (ok) dcopy(D, psi, X);
       } else {
         // guess chi0 = (1 - i tau H) psi ; solve (1 + i tau H) chi = psi ;
         // psi' = (1 - i tau H) chi  (or 2 chi - psi)
-        if (mixed) {
-          guess_mixed(D, tau, psi, X, cnt);
-          ok = solve_mixed(D, P, tau, psi, X, cnt, sc);
-        } else {
-          D.template hpsi<double>(psi, X, nullptr, 0.0, 1.0, mic);
-          cnt.hpsi += 1;
-          ok = solve_fp64(D, P, tau, psi, X, cnt, sc);
-        }
+        ok = implicit_solve<MODE>(D, P, tau, psi, X, mixed, cnt, sc);
         if (ok) {
           if (P.mid_epi) {
             D.template hpsi<double>(X, psi, nullptr, 0.0, 1.0, mic);
