@@ -136,6 +136,11 @@ def fp64_peak_tflops(sm_mhz=None):
     return 152 * 4 * mhz * 1e6 / 1e12
 
 
+def _guess(args):
+    """Start of each implicit solve: 0 = explicit Euler (Sec. II B), 1 = zero."""
+    return 1 if getattr(args, "guess", "euler") == "zero" else 0
+
+
 def shard_seeds(rank, per_rank):
     """Seeds of the wavepackets rank `rank` propagates (weak scaling: every
     rank owns per_rank independent wavepackets; no data is exchanged)."""
@@ -190,7 +195,7 @@ def run_ours(args):
     prec = qg.QG_C64_MIXED if args.precision == "mixed" else qg.QG_C128
     grid, model, states = _setup_batch(qg, wl, B, rank, stream.cuda_stream, prec)
     batch = qg.Batch(states)
-    opts = qg.default_solver_opts(tol=WORKLOAD["tol"], restart=WORKLOAD["restart"], max_iters=600,
+    opts = qg.default_solver_opts(tol=WORKLOAD["tol"], restart=WORKLOAD["restart"], max_iters=600, guess=_guess(args),
                                   solver=qg.QG_SOLVER_LANCZOS if args.solver == "lanczos" else qg.QG_SOLVER_GMRES)
     dt = WORKLOAD["dt_fs"] * FS
     m, o, sc = WORKLOAD["method"], WORKLOAD["order"], WORKLOAD["scheme"]
@@ -267,7 +272,7 @@ def run_ours(args):
                        "method": "implicit midpoint" if m == 1 else "trapezoidal",
                        "order": o, "scheme": "suzuki" if sc == 1 else "triple_jump",
                        "dt_fs": WORKLOAD["dt_fs"], "gmres_tol": WORKLOAD["tol"], "restart": WORKLOAD["restart"],
-                       "precision": args.precision, "solver": args.solver,
+                       "precision": args.precision, "solver": args.solver, "guess": args.guess,
                        "l2": "working set %.0f MB > L2 (129 MB): no flush needed" %
                              (B * (WORKLOAD["restart"] + 6) * len_state * 16 / 1e6)},
             "hpsi_grid_point_applications_per_s": hpsi_rate,
@@ -402,7 +407,7 @@ def run_batched(args):
         states.append(st)
         sizes.append((m["N"], m["S"]))
     batch = qg.Batch(states)
-    opts = qg.default_solver_opts(tol=BATCHED["tol"], restart=BATCHED["restart"])
+    opts = qg.default_solver_opts(tol=BATCHED["tol"], restart=BATCHED["restart"], guess=_guess(args))
     dt = BATCHED["dt_fs"] * FS
     m_, o_, s_ = BATCHED["method"], BATCHED["order"], BATCHED["scheme"]
     tuning = batch.autotune(m_, o_, s_, dt, 1, opts)
@@ -486,7 +491,7 @@ def run_2d(args):
     m = qg.Model(g, 2, list(p["mass"]), W=W, dW=dW)
     q0, p0, s0 = wl.model2d_initial()
     dt = 0.1 * FS
-    opts = qg.default_solver_opts(tol=1e-12,
+    opts = qg.default_solver_opts(tol=1e-12, guess=_guess(args),
                                   solver=qg.QG_SOLVER_LANCZOS if args.solver == "lanczos" else qg.QG_SOLVER_GMRES)
     res = {}
     for name, prec in (("mixed", qg.QG_C64_MIXED), ("fp64", qg.QG_C128)):
@@ -512,7 +517,7 @@ def run_2d(args):
             "scaling": "strong", "vs_baseline": None, "dtype": "c64 inner / f64 residual",
             "data": "synthetic (2-D two-state model)",
             "config": {"workload": "model2d_256x256_midpoint_suzuki6", "grid": list(ns), "S": 2, "order": 6,
-                       "dt_fs": 0.1, "gmres_tol": 1e-12, "solver": args.solver,
+                       "dt_fs": 0.1, "gmres_tol": 1e-12, "solver": args.solver, "guess": args.guess,
                        "launch": "one cooperative launch over all SMs"},
             "fp64_path": {"value": args.steps / (t_f / 1e3), "ms_per_step": t_f / args.steps,
                           "fp64_hpsi": res["fp64"]["stats"]["n_hpsi"]},
@@ -561,7 +566,7 @@ def run_adjoint(args):
     st.set_gaussian(1, [wl.NAI_Q0], [0.0], [wl.NAI_SIGMA0])
     psi0 = torch.tensor(np.stack([st.get()] * nm), device="cuda", requires_grad=True)
     dt, nsteps = 0.5 * FS, args.steps
-    opts = qg.default_solver_opts(tol=1e-12,
+    opts = qg.default_solver_opts(tol=1e-12, guess=_guess(args),
                                   solver=qg.QG_SOLVER_LANCZOS if args.solver == "lanczos" else qg.QG_SOLVER_GMRES)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -626,7 +631,7 @@ def run_sweep(args):
     table = {"verify": SWEEP_VERIFY, "coarse": SWEEP_JOBS, "point": SWEEP_POINT}[args.sweep_set]
     jobs = [(sc, o, n) for (sc, o), ns in table.items() for n in ns]
     jobs.sort(key=lambda j: -j[2] * (3 if j[0] == 0 else 5) ** (j[1] // 2 - 1))
-    opts = qg.default_solver_opts(tol=args.sweep_tol, max_iters=600,
+    opts = qg.default_solver_opts(tol=args.sweep_tol, max_iters=600, guess=_guess(args),
                                   solver=qg.QG_SOLVER_LANCZOS if args.solver == "lanczos" else qg.QG_SOLVER_GMRES)
     outdir = args.sweep_dir
     if outdir:
@@ -677,6 +682,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--guess", default="euler", choices=["euler", "zero"],
+                    help="start of each implicit solve: explicit Euler (Sec. II B) or zero")
     ap.add_argument("--sweep", action="store_true", help="convergence-error sweep that fixes the operating point")
     ap.add_argument("--solver", default="lanczos", choices=["gmres", "lanczos"],
                     help="Krylov method of the implicit steps (same minimal-residual iterates)")
