@@ -55,6 +55,24 @@ FftPlan make_plan(int n) {
   return p;
 }
 
+// Twiddle table in the pass-by-pass layout fft_pass reads: for forward pass
+// i (block length L, radix R, m = L / R) the entries (r - 1) m + j,
+// r = 1..R-1, j = 0..m-1, hold w_L^{j r} = w[j r n / L] (w the natural table
+// exp(-2 pi i k / n)).  The last pass has m = 1 and needs none; the layout
+// has at most n - 1 entries and is padded with 1 to n.
+void pass_twiddles(const FftPlan& p, const std::vector<double2>& w, std::vector<double2>& out) {
+  const int n = p.n;
+  out.assign(n, make_double2(1.0, 0.0));
+  int L = n, off = 0;
+  for (int i = 0; i < p.npass - 1; ++i) {
+    const int R = p.radix[i], m = L / R;
+    for (int r = 1; r < R; ++r)
+      for (int j = 0; j < m; ++j) out[off + (r - 1) * m + j] = w[(size_t)j * r * (n / L)];
+    off += (R - 1) * m;
+    L /= R;
+  }
+}
+
 // Frequency index held at position p after the decimation-in-frequency
 // passes radix[first..]: a block of length len splits into R sub-blocks of
 // length len/R; sub-block q holds the frequencies q + R f' where f' is the
@@ -292,8 +310,9 @@ qg_status qg_create_grid(int D, const int* N, const double* qmin, const double* 
     g->dq[d] = (qmax[d] - qmin[d]) / n;
     g->ntot *= n;
     g->plan[d] = make_plan(n);
-    std::vector<double2> tw;
-    twiddles(n, tw);
+    std::vector<double2> tw_nat, tw;
+    twiddles(n, tw_nat);
+    pass_twiddles(g->plan[d], tw_nat, tw);
     std::vector<int> f;
     freq_positions(n, g->plan[d].radix, g->plan[d].npass, f);
     std::vector<double> kd(n);

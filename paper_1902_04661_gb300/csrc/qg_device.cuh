@@ -181,33 +181,41 @@ __device__ __forceinline__ void dft(C (&x)[RD]) {
   }
 }
 
-// Operands of one H psi evaluation in one precision.
+// Operands of one H psi evaluation in one precision.  The transform of
+// length n = 2^k runs n8 radix-8 passes and then npass - n8 radix-4 passes
+// (decimation in frequency; the inverse runs them backwards).
 template <typename R>
 struct HOp {
   using C = typename Cx<R>::T;
-  int n, S, npass;
-  int radix[QG_MAX_PASSES];
+  int n, S, npass, n8;
   R h2m;
-  const C* tw;   // exp(-2 pi i k / n)
+  const C* tw;   // twiddles, pass by pass (see fft_pass)
   const R* kd;   // k at digit-reversed positions, divided by n
   const R* V;
   const R* F;
   C* U;          // scratch vector (S * n)
 };
 
+// Number of leading radix-8 passes of a plan.
+__host__ __device__ inline int count_radix8(const int* radix, int npass) {
+  int k = 0;
+  while (k < npass && radix[k] == 8) ++k;
+  return k;
+}
+
 // One radix-RD pass over nb vectors of length n in shared memory, in place.
 // Block length L, m = L / RD.  Forward (decimation in frequency): DFT over the
 // RD elements j + r m of a block, then multiply by w_L^{j r}.  Inverse
 // (decimation in time): multiply by conj(w_L^{j r}), then inverse DFT; it
-// undoes the forward pass up to a factor RD.  w_L^{j r} = tw[j r n / L],
-// an index below n.
+// undoes the forward pass up to a factor RD.  twp is this pass's segment of
+// the twiddle table: twp[(r - 1) m + j] = w_L^{j r}, so consecutive j (the
+// lanes of a warp) read consecutive entries.
 template <int RD, bool INV, typename C>
-__device__ __forceinline__ void fft_pass(C* buf, int n, int nb, int L, const C* __restrict__ tw) {
+__device__ __forceinline__ void fft_pass(C* buf, int n, int nb, int L, const C* __restrict__ twp) {
   const int lm = ilog2(L / RD);
   const int m = 1 << lm;
   const int lpv = ilog2(n / RD);
   const int total = nb << lpv;
-  const int tshift = ilog2(n / L);
   for (int b = threadIdx.x; b < total; b += kThreads) {
     const int v = b >> lpv;
     const int bb = b & ((n / RD) - 1);
@@ -221,12 +229,12 @@ __device__ __forceinline__ void fft_pass(C* buf, int n, int nb, int L, const C* 
       dft<RD, false>(x);
       if (j) {
 #pragma unroll
-        for (int r = 1; r < RD; ++r) x[r] = cmul(x[r], __ldg(tw + ((j * r) << tshift)));
+        for (int r = 1; r < RD; ++r) x[r] = cmul(x[r], __ldg(twp + (r - 1) * m + j));
       }
     } else {
       if (j) {
 #pragma unroll
-        for (int r = 1; r < RD; ++r) x[r] = cmulc(x[r], __ldg(tw + ((j * r) << tshift)));
+        for (int r = 1; r < RD; ++r) x[r] = cmulc(x[r], __ldg(twp + (r - 1) * m + j));
       }
       dft<RD, true>(x);
     }
@@ -258,52 +266,51 @@ __device__ __forceinline__ void fft_center(C* buf, int n, int nb, const R* __res
   }
 }
 
-template <bool INV, typename C>
-__device__ __forceinline__ void fft_pass_dispatch(int RD, C* buf, int n, int nb, int L, const C* tw) {
-  if (RD == 8)
-    fft_pass<8, INV>(buf, n, nb, L, tw);
-  else if (RD == 4)
-    fft_pass<4, INV>(buf, n, nb, L, tw);
-  else
-    fft_pass<2, INV>(buf, n, nb, L, tw);
-}
-
 // buf <- D buf for nb vectors (spectral first derivative, Sec. II D):
 // forward FFT, multiply by i k, inverse FFT (1/n folded into kd).
 template <typename R>
 __device__ __forceinline__ void spectral_derivative(typename Cx<R>::T* buf, int nb, const HOp<R>& H) {
-  const int n = H.n;
-  int L = n;
-  for (int i = 0; i < H.npass - 1; ++i) {
-    fft_pass_dispatch<false>(H.radix[i], buf, n, nb, L, H.tw);
-    L /= H.radix[i];
+  using C = typename Cx<R>::T;
+  const int n = H.n, np = H.npass, n8 = H.n8;
+  const C* tw = H.tw;
+  const R* kd = H.kd;
+  int L = n, off = 0;
+  for (int i = 0; i < np - 1; ++i) {
+    const int RD = i < n8 ? 8 : 4;
+    if (RD == 8)
+      fft_pass<8, false>(buf, n, nb, L, tw + off);
+    else
+      fft_pass<4, false>(buf, n, nb, L, tw + off);
+    off += (RD - 1) * (L / RD);
+    L /= RD;
     __syncthreads();
   }
-  const int Rc = H.radix[H.npass - 1];
-  if (Rc == 8)
-    fft_center<8>(buf, n, nb, H.kd);
-  else if (Rc == 4)
-    fft_center<4>(buf, n, nb, H.kd);
+  if (np - 1 < n8)
+    fft_center<8>(buf, n, nb, kd);
   else
-    fft_center<2>(buf, n, nb, H.kd);
+    fft_center<4>(buf, n, nb, kd);
   __syncthreads();
-  for (int i = H.npass - 2; i >= 0; --i) {
-    L *= H.radix[i];
-    fft_pass_dispatch<true>(H.radix[i], buf, n, nb, L, H.tw);
+  for (int i = np - 2; i >= 0; --i) {
+    const int RD = i < n8 ? 8 : 4;
+    L *= RD;
+    off -= (RD - 1) * (L / RD);
+    if (RD == 8)
+      fft_pass<8, true>(buf, n, nb, L, tw + off);
+    else
+      fft_pass<4, true>(buf, n, nb, L, tw + off);
     __syncthreads();
   }
 }
 
-// Coupling F_{st}(q_j) from the stored upper triangle.
+// Coupling F_{st}(q_j) from the stored upper triangle (S(S-1)/2 rows of n).
 template <typename R>
-__device__ __forceinline__ R coupling(const HOp<R>& H, int s, int t, int j) {
-  const int S = H.S;
+__device__ __forceinline__ R coupling(const R* __restrict__ F, int n, int S, int s, int t, int j) {
   if (s < t) {
     const int p = s * S - (s * (s + 1)) / 2 + (t - s - 1);
-    return __ldg(H.F + (size_t)p * H.n + j);
+    return __ldg(F + (size_t)p * n + j);
   } else {
     const int p = t * S - (t * (t + 1)) / 2 + (s - t - 1);
-    return -__ldg(H.F + (size_t)p * H.n + j);
+    return -__ldg(F + (size_t)p * n + j);
   }
 }
 
@@ -323,6 +330,8 @@ __device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T
   const int n = H.n, S = H.S;
   const int ln = ilog2(n);
   C* U = H.U;
+  const R* F = H.F;
+  const R* V = H.V;
   const int nb = (S <= nb_cap) ? S : 1;
   // U = (D + F) x
   for (int s0 = 0; s0 < S; s0 += nb) {
@@ -333,7 +342,7 @@ __device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T
       const int s = s0 + (i >> ln), j = i & (n - 1);
       C acc = sbuf[spad<C>(i)];
       for (int t = 0; t < S; ++t)
-        if (t != s) acc = caxpy_r(coupling(H, s, t, j), x[t * n + j], acc);
+        if (t != s) acc = caxpy_r(coupling(F, n, S, s, t, j), x[t * n + j], acc);
       U[s * n + j] = acc;
     }
     __syncthreads();
@@ -348,9 +357,9 @@ __device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T
       const int s = s0 + (i >> ln), j = i & (n - 1);
       C acc = sbuf[spad<C>(i)];
       for (int t = 0; t < S; ++t)
-        if (t != s) acc = caxpy_r(coupling(H, s, t, j), U[t * n + j], acc);
+        if (t != s) acc = caxpy_r(coupling(F, n, S, s, t, j), U[t * n + j], acc);
       const C xs = x[s * n + j];
-      const R v = __ldg(H.V + s * n + j);
+      const R v = __ldg(V + s * n + j);
       const C hx = cmk<C>(fma(mh, acc.x, v * xs.x), fma(mh, acc.y, v * xs.y));
       C out = caxpy(c, hx, cmk<C>(a * xs.x, a * xs.y));
       if (e != (R)0) out = caxpy_r(e, z[s * n + j], out);
@@ -368,6 +377,7 @@ __device__ __forceinline__ void apply_d_plus_f(const HOp<R>& H, typename Cx<R>::
   using C = typename Cx<R>::T;
   const int n = H.n, S = H.S;
   const int ln = ilog2(n);
+  const R* F = H.F;
   const int nb = (S <= nb_cap) ? S : 1;
   for (int s0 = 0; s0 < S; s0 += nb) {
     for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[spad<C>(i)] = x[s0 * n + i];
@@ -377,7 +387,7 @@ __device__ __forceinline__ void apply_d_plus_f(const HOp<R>& H, typename Cx<R>::
       const int s = s0 + (i >> ln), j = i & (n - 1);
       C acc = sbuf[spad<C>(i)];
       for (int t = 0; t < S; ++t)
-        if (t != s) acc = caxpy_r(coupling(H, s, t, j), x[t * n + j], acc);
+        if (t != s) acc = caxpy_r(coupling(F, n, S, s, t, j), x[t * n + j], acc);
       y[s * n + j] = acc;
     }
     __syncthreads();

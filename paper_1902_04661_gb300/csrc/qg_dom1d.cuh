@@ -34,7 +34,7 @@ __device__ __forceinline__ HOp<double> hop64(const InstDesc& I, double2* U) {
   H.n = I.n;
   H.S = I.S;
   H.npass = I.npass;
-  for (int i = 0; i < QG_MAX_PASSES; ++i) H.radix[i] = I.radix[i];
+  H.n8 = count_radix8(I.radix, I.npass);
   H.h2m = I.h2m;
   H.tw = I.tw;
   H.kd = I.kd;
@@ -49,7 +49,7 @@ __device__ __forceinline__ HOp<float> hop32(const InstDesc& I, float2* U) {
   H.n = I.n;
   H.S = I.S;
   H.npass = I.npass;
-  for (int i = 0; i < QG_MAX_PASSES; ++i) H.radix[i] = I.radix[i];
+  H.n8 = count_radix8(I.radix, I.npass);
   H.h2m = (float)I.h2m;
   H.tw = I.tw32;
   H.kd = I.kd32;
@@ -61,6 +61,7 @@ __device__ __forceinline__ HOp<float> hop32(const InstDesc& I, float2* U) {
 
 // One CTA owns one whole 1-D instance.
 struct Dom1D {
+  static constexpr bool kFusedDots = false;   // CTA-local sums are cheap: reduce them separately
   int len;
   double dv;
   unsigned char* gm;

@@ -16,16 +16,29 @@
 
 namespace qg {
 
+static __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+static __device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Bounded sense-reversing grid barrier (all CTAs are co-resident under the
-// cooperative launch).  A CTA that waits more than about a second gives up,
-// raises the error flag and returns false; every later barrier then fails
-// too, so every CTA leaves the kernel.
+// cooperative launch).  Thread 0 of each CTA publishes the CTA's writes,
+// arrives on a counter, and polls the generation word with acquire loads.
+// A CTA that waits more than about a second gives up, raises the error flag
+// and returns false; every later barrier then fails too, so every CTA leaves
+// the kernel.
 static __device__ bool grid_barrier(unsigned* bar, int* err) {
   __shared__ int s_fail;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
+    const unsigned g = ld_acquire_gpu(bar + 1);
     __threadfence();
     const unsigned arrived = atomicAdd(bar, 1u) + 1u;
     int fail = 0;
@@ -34,22 +47,23 @@ static __device__ bool grid_barrier(unsigned* bar, int* err) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
-      long long spins = 0;
-      while (*gen == g) {
-        if (++spins > (1LL << 24)) {
-          fail = 1;
-          atomicExch(err, 1);
-          break;
+      const unsigned long long t0 = globaltimer_ns();
+      for (long long spins = 1; ld_acquire_gpu(bar + 1) == g; ++spins) {
+        if ((spins & 31) == 0) {
+          if (ld_acquire_gpu(reinterpret_cast<const unsigned*>(err))) {   // another CTA already gave up
+            fail = 1;
+            break;
+          }
+          if (globaltimer_ns() - t0 > 1000000000ull || spins > (1LL << 23)) {
+            fail = 1;
+            atomicExch(err, 1);
+            break;
+          }
         }
-        if (*(volatile int*)err) {   // another CTA already gave up
-          fail = 1;
-          break;
-        }
-        __nanosleep(64);
       }
     }
     __threadfence();
-    if (*(volatile int*)err) fail = 1;
+    if (ld_acquire_gpu(reinterpret_cast<const unsigned*>(err))) fail = 1;
     s_fail = fail;
   }
   __syncthreads();
@@ -57,6 +71,9 @@ static __device__ bool grid_barrier(unsigned* bar, int* err) {
 }
 
 struct Dom2D {
+  // H psi can form Re<x, y> and ||y||^2 in its last pass and reduce them
+  // across the grid in its closing barrier (see hpsi)
+  static constexpr bool kFusedDots = true;
   const Inst2D* I;
   int len, N, n0, n1, S;
   int r_lo, r_hi, c_lo, c_hi;
@@ -86,6 +103,23 @@ struct Dom2D {
     }
   }
 
+  // Adds the per-CTA partial sums buf[b * 32 + k], b < gridDim.x, k < K:
+  // warp w handles k = w, w + kWarps, ..., loads 32 partials at a time and
+  // reduces with a fixed shuffle tree, so every CTA forms the same values in
+  // the same order.
+  template <int K, typename R>
+  __device__ __forceinline__ void gather(const R* buf, R* out) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = w; k < K; k += kWarps) {
+      R s = 0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(buf + b * 32 + k);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) out[k] = s;
+    }
+    __syncthreads();
+  }
+
   template <int K, typename R>
   __device__ __forceinline__ bool sum(R (&v)[K], R* out) {
     cta_sum<K>(v, reinterpret_cast<R*>(red), out);
@@ -93,21 +127,19 @@ struct Dom2D {
     parity ^= 1;
     if (threadIdx.x < K) buf[blockIdx.x * 32 + threadIdx.x] = out[threadIdx.x];
     good = good && grid_barrier(I->bar, I->err);
-    if (threadIdx.x < K) {
-      R s = 0;
-      for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(buf + b * 32 + threadIdx.x);
-      out[threadIdx.x] = s;
-    }
-    __syncthreads();
+    gather<K>(buf, out);
     return good;
   }
 
   __device__ __forceinline__ bool ok() const { return good; }
 
   // y = e z + a x + c (H x), H = sum_d -hbar^2/2m_d (D_d + F_d)^2 + V.
+  // With dots (shared memory, 2 values): also dots[0] = sum Re(conj(x) y)
+  // and dots[1] = sum |y|^2 over the whole grid (without the grid weight),
+  // reduced in the closing grid barrier; every CTA gets the same values.
   template <typename R>
   __device__ void hpsi(const typename Cx<R>::T* x, typename Cx<R>::T* y, const typename Cx<R>::T* z, R e, R a,
-                       typename Cx<R>::T c) {
+                       typename Cx<R>::T c, R* dots = nullptr) {
     using C = typename Cx<R>::T;
     C* sb = reinterpret_cast<C*>(fb);
     const HOp<R>* H = nullptr;
@@ -179,6 +211,7 @@ struct Dom2D {
     good = good && grid_barrier(I->bar, I->err);
     // ---- dimension 0 (columns, stride n1): y = e z + a x + c (T - h2m_0 (D_0 + F_0)^2 x).
     // All owned columns and surfaces form one batch: vector (col_local * S + s).
+    R pd[2] = {(R)0, (R)0};
     {
       const HOp<R>& H0 = H[0];
       const R mh = -(R)I->h2m[0];
@@ -221,12 +254,25 @@ struct Dom2D {
           C out = caxpy(c, hx, cmk<C>(a * xs.x, a * xs.y));
           if (e != (R)0) out = caxpy_r(e, z[(size_t)s * N + p], out);
           y[(size_t)s * N + p] = out;
+          if (dots) {
+            pd[0] = fma(xs.x, out.x, fma(xs.y, out.y, pd[0]));
+            pd[1] = fma(out.x, out.x, fma(out.y, out.y, pd[1]));
+          }
         }
       }
       __syncthreads();
       }
     }
+    R* buf = reinterpret_cast<R*>(I->gred + (size_t)parity * gridDim.x * 32);
+    if (dots) {
+      cta_sum<2>(pd, reinterpret_cast<R*>(red), dots);
+      if (threadIdx.x < 2) buf[blockIdx.x * 32 + threadIdx.x] = dots[threadIdx.x];
+    }
     good = good && grid_barrier(I->bar, I->err);
+    if (dots) {
+      gather<2>(buf, dots);
+      parity ^= 1;
+    }
   }
 
   // F_{st} at flattened point p from one dimension's upper triangle.
@@ -263,14 +309,14 @@ static __device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_
     D.H64[d].n = I.n[d];
     D.H64[d].S = I.S;
     D.H64[d].npass = I.npass[d];
-    for (int i = 0; i < QG_MAX_PASSES; ++i) D.H64[d].radix[i] = I.radix[d][i];
+    D.H64[d].n8 = count_radix8(I.radix[d], I.npass[d]);
     D.H64[d].h2m = I.h2m[d];
     D.H64[d].tw = I.tw[d];
     D.H64[d].kd = I.kd[d];
     D.H32[d].n = I.n[d];
     D.H32[d].S = I.S;
     D.H32[d].npass = I.npass[d];
-    for (int i = 0; i < QG_MAX_PASSES; ++i) D.H32[d].radix[i] = I.radix[d][i];
+    D.H32[d].n8 = count_radix8(I.radix[d], I.npass[d]);
     D.H32[d].h2m = (float)I.h2m[d];
     D.H32[d].tw = I.tw32[d];
     D.H32[d].kd = I.kd32[d];

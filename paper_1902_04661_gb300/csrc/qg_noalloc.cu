@@ -29,15 +29,28 @@ constexpr size_t kNaBytes = kNaWorkBytes + kNaTwBytes + kNaKdBytes + kNaStatByte
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
-// Twiddles exp(-2 pi i k / n) and the wave numbers of the digit-reversed
-// positions (divided by n), for the radix plan in `plan`.
+// Twiddles of the radix plan in `plan`, pass by pass (the layout fft_pass
+// reads: for forward pass i with block length L, radix R and m = L / R,
+// entry (r - 1) m + j holds exp(-2 pi i j r / L)), and the wave numbers of
+// the digit-reversed positions (divided by n).
 __global__ void noalloc_tables_kernel(unsigned char* base, FftPlan plan, double dq) {
   const int n = plan.n;
   double2* tw = reinterpret_cast<double2*>(base + kNaWorkBytes);
   double* kd = reinterpret_cast<double*>(base + kNaWorkBytes + kNaTwBytes);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    int L = n, off = 0, e = 0;
+    for (int i = 0; i < plan.npass - 1; ++i) {
+      const int R = plan.radix[i], m = L / R, seg = (R - 1) * m;
+      if (k < off + seg) {
+        const int r = (k - off) / m + 1, j = (k - off) - (r - 1) * m;
+        e = j * r * (n / L);
+        break;
+      }
+      off += seg;
+      L /= R;
+    }
     double s, c;
-    sincospi(2.0 * (double)k / (double)n, &s, &c);
+    sincospi(2.0 * (double)e / (double)n, &s, &c);
     tw[k] = make_double2(c, -s);
     // frequency held at position k after the decimation-in-frequency passes
     int f = 0, mult = 1, rem = k, len = n;

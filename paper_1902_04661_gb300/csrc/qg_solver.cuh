@@ -331,21 +331,28 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
   int total = 0;
   for (int guard = 0; guard < P.max_iters + 2; ++guard) {
     // r = b - A X  (= b on the first pass when X starts at zero)
+    R beta1;
     if (guard == 0 && P.x0_zero) {
       D.each([&](int i) { Vc[i] = b[i]; });
       __syncthreads();
+      beta1 = bn;
+    } else if constexpr (Dom::kFusedDots) {
+      D.template hpsi<R>(X, Vc, b, (R)1, (R)-1, mic, sc);
+      count_hpsi<R>(cnt);
+      if (!D.ok()) return false;
+      beta1 = sqrt(dv * sc[1]);
     } else {
       D.template hpsi<R>(X, Vc, b, (R)1, (R)-1, mic);
       count_hpsi<R>(cnt);
+      R rv[1] = {0};
+      D.each([&](int i) {
+        const C a = Vc[i];
+        rv[0] = fma(a.x, a.x, fma(a.y, a.y, rv[0]));
+      });
+      if (!D.template sum<1>(rv, sc)) return false;
+      beta1 = sqrt(dv * sc[0]);
     }
     if (guard > 0) cnt.restart++;
-    R rv[1] = {0};
-    D.each([&](int i) {
-      const C a = Vc[i];
-      rv[0] = fma(a.x, a.x, fma(a.y, a.y, rv[0]));
-    });
-    if (!D.template sum<1>(rv, sc)) return false;
-    const R beta1 = sqrt(dv * sc[0]);
     if (beta1 <= target || bn == (R)0) {
       *res_out = (bn > (R)0) ? (double)(beta1 / bn) : 0.0;
       if (total > cnt.max_krylov) cnt.max_krylov = total;
@@ -366,27 +373,43 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
     R res_est = beta1;
     bool conv = false;
     for (int k = 1; total < P.max_iters; ++k) {
-      // Wn = H Vc - beta_k Vp
-      if (k == 1)
-        D.template hpsi<R>(Vc, Wn, nullptr, (R)0, (R)0, cmk<C>((R)1, (R)0));
-      else
-        D.template hpsi<R>(Vc, Wn, Vp, -betak, (R)0, cmk<C>((R)1, (R)0));
-      count_hpsi<R>(cnt);
-      R av[1] = {0};
-      D.each([&](int i) {
-        const C v = Vc[i], w = Wn[i];
-        av[0] = fma(v.x, w.x, fma(v.y, w.y, av[0]));
-      });
-      if (!D.template sum<1>(av, sc)) return false;
-      const R alpha = dv * sc[0];
-      R wv[1] = {0};
-      D.each([&](int i) {
-        const C w = caxpy_r(-alpha, Vc[i], Wn[i]);
-        Wn[i] = w;
-        wv[0] = fma(w.x, w.x, fma(w.y, w.y, wv[0]));
-      });
-      if (!D.template sum<1>(wv, sc)) return false;
-      const R betan = sqrt(dv * sc[0]);
+      // Wn = H Vc - beta_k Vp ; alpha = <Vc, Wn> ; beta_{k+1} = ||Wn - alpha Vc||
+      R alpha, betan;
+      if constexpr (Dom::kFusedDots) {
+        // one grid-wide reduction per iteration, inside H psi:
+        // ||Wn - alpha Vc||^2 = ||Wn||^2 - alpha^2 (||Vc|| = 1, Vc _|_ Vp);
+        // Wn - alpha Vc is formed in the update pass below
+        if (k == 1)
+          D.template hpsi<R>(Vc, Wn, nullptr, (R)0, (R)0, cmk<C>((R)1, (R)0), sc);
+        else
+          D.template hpsi<R>(Vc, Wn, Vp, -betak, (R)0, cmk<C>((R)1, (R)0), sc);
+        count_hpsi<R>(cnt);
+        if (!D.ok()) return false;
+        alpha = dv * sc[0];
+        const R w2 = dv * sc[1] - alpha * alpha;
+        betan = w2 > (R)0 ? sqrt(w2) : (R)0;
+      } else {
+        if (k == 1)
+          D.template hpsi<R>(Vc, Wn, nullptr, (R)0, (R)0, cmk<C>((R)1, (R)0));
+        else
+          D.template hpsi<R>(Vc, Wn, Vp, -betak, (R)0, cmk<C>((R)1, (R)0));
+        count_hpsi<R>(cnt);
+        R av[1] = {0};
+        D.each([&](int i) {
+          const C v = Vc[i], w = Wn[i];
+          av[0] = fma(v.x, w.x, fma(v.y, w.y, av[0]));
+        });
+        if (!D.template sum<1>(av, sc)) return false;
+        alpha = dv * sc[0];
+        R wv[1] = {0};
+        D.each([&](int i) {
+          const C w = caxpy_r(-alpha, Vc[i], Wn[i]);
+          Wn[i] = w;
+          wv[0] = fma(w.x, w.x, fma(w.y, w.y, wv[0]));
+        });
+        if (!D.template sum<1>(wv, sc)) return false;
+        betan = sqrt(dv * sc[0]);
+      }
       // column k of [I; 0] + i tau T: rows k-1, k, k+1
       C eps = cmk<C>((R)0, (R)0);
       C del = cmk<C>((R)0, tau * betak);
@@ -427,13 +450,17 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
       const C ir = cmk<C>(r.x * rr, -r.y * rr);
       const R ibn = betan > (R)0 ? (R)1 / betan : (R)0;
       D.each([&](int i) {
-        C d = Vc[i];
+        const C v = Vc[i];
+        C d = v;
         d = cnaxpy(del, Dp[i], d);
         d = cnaxpy(eps, Dq[i], d);
         d = cmul(d, ir);
         Dq[i] = d;                                   // newest direction, in the oldest slot
         X[i] = caxpy(gk, d, X[i]);
-        Wn[i] = cscale(ibn, Wn[i]);                  // v_{k+1}
+        if constexpr (Dom::kFusedDots)
+          Wn[i] = cscale(ibn, caxpy_r(-alpha, v, Wn[i]));   // v_{k+1} (alpha Vc removed here)
+        else
+          Wn[i] = cscale(ibn, Wn[i]);                       // v_{k+1}
       });
       __syncthreads();
       C* t0 = Dq;
@@ -519,20 +546,27 @@ __device__ bool solve_mixed(Dom& D, const StepPlan& P, double tau, const double2
   const double target = P.tol * bn;
   SolveParams sp{P.inner_tol, P.restart, P.max_iters, P.reorth, 0, P.solver, 1};
   for (int outer = 0; outer <= P.max_outer; ++outer) {
+    double rho;
     if (outer == 0 && x0_zero) {
       D.each([&](int i) { Rv[i] = b[i]; });
       __syncthreads();
+      rho = bn;
+    } else if constexpr (Dom::kFusedDots) {
+      D.template hpsi<double>(X, Rv, b, 1.0, -1.0, mic, sc);
+      cnt.hpsi++;
+      if (!D.ok()) return false;
+      rho = sqrt(dv * sc[1]);
     } else {
       D.template hpsi<double>(X, Rv, b, 1.0, -1.0, mic);
       cnt.hpsi++;
+      double rv[1] = {0.0};
+      D.each([&](int i) {
+        const double2 a = Rv[i];
+        rv[0] = fma(a.x, a.x, fma(a.y, a.y, rv[0]));
+      });
+      if (!D.template sum<1>(rv, sc)) return false;
+      rho = sqrt(dv * sc[0]);
     }
-    double rv[1] = {0.0};
-    D.each([&](int i) {
-      const double2 a = Rv[i];
-      rv[0] = fma(a.x, a.x, fma(a.y, a.y, rv[0]));
-    });
-    if (!D.template sum<1>(rv, sc)) return false;
-    const double rho = sqrt(dv * sc[0]);
     if (rho <= target || bn == 0.0) {
       const double r = bn > 0.0 ? rho / bn : 0.0;
       if (r > cnt.max_res) cnt.max_res = r;
