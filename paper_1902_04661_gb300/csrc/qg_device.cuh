@@ -209,7 +209,8 @@ __host__ __device__ inline int count_radix8(const int* radix, int npass) {
 // (decimation in time): multiply by conj(w_L^{j r}), then inverse DFT; it
 // undoes the forward pass up to a factor RD.  twp is this pass's segment of
 // the twiddle table: twp[(r - 1) m + j] = w_L^{j r}, so consecutive j (the
-// lanes of a warp) read consecutive entries.
+// lanes of a warp) read consecutive entries.  The tables are read with
+// generic loads: they may sit in global or in shared memory.
 template <int RD, bool INV, typename C>
 __device__ __forceinline__ void fft_pass(C* buf, int n, int nb, int L, const C* __restrict__ twp) {
   const int lm = ilog2(L / RD);
@@ -229,12 +230,12 @@ __device__ __forceinline__ void fft_pass(C* buf, int n, int nb, int L, const C* 
       dft<RD, false>(x);
       if (j) {
 #pragma unroll
-        for (int r = 1; r < RD; ++r) x[r] = cmul(x[r], __ldg(twp + (r - 1) * m + j));
+        for (int r = 1; r < RD; ++r) x[r] = cmul(x[r], twp[(r - 1) * m + j]);
       }
     } else {
       if (j) {
 #pragma unroll
-        for (int r = 1; r < RD; ++r) x[r] = cmulc(x[r], __ldg(twp + (r - 1) * m + j));
+        for (int r = 1; r < RD; ++r) x[r] = cmulc(x[r], twp[(r - 1) * m + j]);
       }
       dft<RD, true>(x);
     }
@@ -257,7 +258,7 @@ __device__ __forceinline__ void fft_center(C* buf, int n, int nb, const R* __res
     dft<RD, false>(x);
 #pragma unroll
     for (int r = 0; r < RD; ++r) {
-      const R k = __ldg(kd + pos + r);
+      const R k = kd[pos + r];
       x[r] = cmk<C>(-k * x[r].y, k * x[r].x);
     }
     dft<RD, true>(x);

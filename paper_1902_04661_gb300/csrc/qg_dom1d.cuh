@@ -76,9 +76,13 @@ struct Dom1D {
   float2* d32;
   float2* basis32;
 
+  // The loop bound is copied to a register: the stores f makes through
+  // generic pointers could otherwise alias *this and force a reload of len
+  // from local memory every iteration.
   template <class F>
   __device__ __forceinline__ void each(F&& f) {
-    for (int i = threadIdx.x; i < len; i += kThreads) f(i);
+    const int n = len;
+    for (int i = threadIdx.x; i < n; i += kThreads) f(i);
   }
   template <int K, typename R>
   __device__ __forceinline__ bool sum(R (&v)[K], R* out) {

@@ -92,14 +92,15 @@ struct Dom2D {
   bool good;
   int cap_elems;   // complex values one shared-memory FFT batch may hold
 
+  // Every point of the owned rows, all surfaces.  Members are copied to
+  // registers first (stores through generic pointers in f could alias *this).
   template <class F>
   __device__ __forceinline__ void each(F&& f) {
-    const int rows = r_hi - r_lo;
-    const int per = rows * n1;
-    const int tot = S * per;
-    for (int k = threadIdx.x; k < tot; k += kThreads) {
-      const int s = k / per;
-      f(s * N + r_lo * n1 + (k - s * per));
+    const int per = (r_hi - r_lo) * n1;
+    const int ns = S, stride = N, first = r_lo * n1;
+    for (int s = 0; s < ns; ++s) {
+      const int base = s * stride + first;
+      for (int k = threadIdx.x; k < per; k += kThreads) f(base + k);
     }
   }
 
@@ -141,6 +142,11 @@ struct Dom2D {
   __device__ void hpsi(const typename Cx<R>::T* x, typename Cx<R>::T* y, const typename Cx<R>::T* z, R e, R a,
                        typename Cx<R>::T c, R* dots = nullptr) {
     using C = typename Cx<R>::T;
+    // members in registers: the stores below go through generic pointers
+    // that could alias *this, which would force reloads from local memory
+    const int n0 = this->n0, n1 = this->n1, N = this->N, S = this->S;
+    const int r_lo = this->r_lo, r_hi = this->r_hi, c_lo = this->c_lo, c_hi = this->c_hi;
+    const int cap_elems = this->cap_elems;
     C* sb = reinterpret_cast<C*>(fb);
     const HOp<R>* H = nullptr;
     C* U;
@@ -287,7 +293,18 @@ struct Dom2D {
   }
 };
 
-static __device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_bytes, double* red) {
+// Shared-memory copy of both dimensions' FFT tables: FP64 twiddles, FP64
+// wave numbers, FP32 twiddles, FP32 wave numbers, each dimension 0 then 1
+// (36 (n0 + n1) bytes).  The 2-D units read global memory through L2 only,
+// so tables kept in global memory would cost an L2 round trip every pass.
+__host__ __device__ inline size_t tables2d_bytes(int n0, int n1) {
+  return ((size_t)36 * (n0 + n1) + 15) / 16 * 16;
+}
+
+// tab_off > 0: the tables are copied to dyn + tab_off (16-byte aligned) and
+// the transforms read them from there.
+static __device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_bytes, double* red,
+                                   int tab_off = 0) {
   Dom2D D;
   D.I = &I;
   D.n0 = I.n[0];
@@ -320,6 +337,30 @@ static __device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_
     D.H32[d].h2m = (float)I.h2m[d];
     D.H32[d].tw = I.tw32[d];
     D.H32[d].kd = I.kd32[d];
+  }
+  if (tab_off > 0) {
+    const int nt = D.n0 + D.n1;
+    unsigned char* t = dyn + tab_off;
+    double2* tw64 = reinterpret_cast<double2*>(t);
+    double* kd64 = reinterpret_cast<double*>(t + (size_t)16 * nt);
+    float2* tw32 = reinterpret_cast<float2*>(t + (size_t)24 * nt);
+    float* kd32 = reinterpret_cast<float*>(t + (size_t)32 * nt);
+    int base = 0;
+    for (int d = 0; d < 2; ++d) {
+      const int n = I.n[d];
+      for (int i = threadIdx.x; i < n; i += kThreads) {
+        tw64[base + i] = I.tw[d][i];
+        kd64[base + i] = I.kd[d][i];
+        tw32[base + i] = I.tw32[d][i];
+        kd32[base + i] = I.kd32[d][i];
+      }
+      D.H64[d].tw = tw64 + base;
+      D.H64[d].kd = kd64 + base;
+      D.H32[d].tw = tw32 + base;
+      D.H32[d].kd = kd32 + base;
+      base += n;
+    }
+    __syncthreads();
   }
   const size_t len = D.len;
   // FP64 workspace: U, T, B, X, P0, basis (m + 1); the mixed form keeps its

@@ -9,12 +9,12 @@
 namespace qg {
 
 // out = H psi (c = 1) or <psi|H|psi> (energy != null).
-__global__ void __launch_bounds__(QG_THREADS, 1) apply_h2d_kernel(const Inst2D I, int fft_bytes, double2* out,
-                                                                  double* energy) {
+__global__ void __launch_bounds__(QG_THREADS, 1) apply_h2d_kernel(const Inst2D I, int fft_bytes, int tab_off,
+                                                                  double2* out, double* energy) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ double red[kWarps * 16];
   __shared__ double sc[64];
-  Dom2D D = make_dom2d(I, dyn, fft_bytes, red);
+  Dom2D D = make_dom2d(I, dyn, fft_bytes, red, tab_off);
   D.hpsi<double>(I.psi, out, nullptr, 0.0, 0.0, make_double2(1.0, 0.0));
   if (energy) {
     double v[2] = {0.0, 0.0};
@@ -131,16 +131,31 @@ static cudaError_t coop_launch(const void* fn, int G, size_t smem, void** args, 
   return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(QG_THREADS), args, smem, st);
 }
 
+// The FFT tables go to shared memory after the kernel's other arrays when
+// the total stays within 200 KB; otherwise they are read from global memory
+// (tab_off = 0).
+static size_t with_tables(const Inst2D& I, size_t smem, int* tab_off) {
+  const size_t off = (smem + 15) / 16 * 16;
+  const size_t tab = qg::tables2d_bytes(I.n[0], I.n[1]);
+  if (off + tab > (size_t)200 * 1024) {
+    *tab_off = 0;
+    return smem;
+  }
+  *tab_off = (int)off;
+  return off + tab;
+}
+
 cudaError_t qg_launch_propagate2d(const Inst2D& I, const StepPlan& P, qg_step_stats* d_stats, cudaStream_t st) {
   const int G = qg_grid2d_ctas(I);
   int fft = (int)fft2d_bytes(I);
-  const size_t smem = fft + qg::gmres_smem_bytes(P.restart);
+  int tab_off = 0;
+  const size_t smem = with_tables(I, fft + qg::gmres_smem_bytes(P.restart), &tab_off);
   cudaError_t e = cudaMemsetAsync(I.bar, 0, 2 * sizeof(unsigned), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.err, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   Inst2D Ic = I;
   StepPlan Pc = P;
-  void* args[] = {&Ic, &Pc, &fft, &d_stats};
+  void* args[] = {&Ic, &Pc, &fft, &tab_off, &d_stats};
   const void* fn = I.precision == QG_C64_MIXED ? qg_propagate2d_fn<1>() : qg_propagate2d_fn<0>();
   return coop_launch(fn, G, smem, args, st);
 }
@@ -148,12 +163,13 @@ cudaError_t qg_launch_propagate2d(const Inst2D& I, const StepPlan& P, qg_step_st
 cudaError_t qg_launch_apply_h2d(const Inst2D& I, double2* d_out, double* d_energy, cudaStream_t st) {
   const int G = qg_grid2d_ctas(I);
   int fft = (int)fft2d_bytes(I);
-  const size_t smem = fft + qg::gmres_smem_bytes(1);
+  int tab_off = 0;
+  const size_t smem = with_tables(I, fft + qg::gmres_smem_bytes(1), &tab_off);
   cudaError_t e = cudaMemsetAsync(I.bar, 0, 2 * sizeof(unsigned), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.err, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   Inst2D Ic = I;
-  void* args[] = {&Ic, &fft, &d_out, &d_energy};
+  void* args[] = {&Ic, &fft, &tab_off, &d_out, &d_energy};
   return coop_launch((const void*)qg::apply_h2d_kernel, G, smem, args, st);
 }
 
