@@ -136,6 +136,20 @@ def fp64_peak_tflops(sm_mhz=None):
     return 152 * 4 * mhz * 1e6 / 1e12
 
 
+# DRAM bytes (read + write) of one propagate_kernel launch of the default
+# workload (FP64, Lanczos, Euler start, one wavepacket per SM), from one ncu
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum).
+# Reported only for that configuration; it must be re-measured whenever the
+# kernel changes.
+NCU_TRAFFIC_BYTES = 3.328174e9 + 16.556524e9
+
+
+def _traffic(args, B):
+    default = (args.precision == "fp64" and args.solver == "lanczos" and _guess(args) == 0 and B == 152
+               and getattr(args, "workload", "nai") == "nai")
+    return NCU_TRAFFIC_BYTES if default else None
+
+
 def _guess(args):
     """Start of each implicit solve: 0 = explicit Euler (Sec. II B), 1 = zero.
     Default: the paper's Euler start, except for the 2-D workload, where the
@@ -292,7 +306,7 @@ def run_ours(args):
             "c64_hpsi_per_substep": sum(s["n_hpsi32"] for s in flat) / max(1, n_sub),
             "hbm_frac_if_streamed": abytes / avg_launch_s / 1e9 / mp.get("hbm_gbs", 6695.2),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": _traffic(args, B),
                          "kernel": "qg::propagate_kernel",
                          "peak_source": "FP64 FMA peak 152 SMs x 4 flop/clk x 2070 MHz (measured 2 DFMA/SM/clk)"},
             "gpu_launches": args.steps,
