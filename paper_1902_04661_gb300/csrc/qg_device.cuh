@@ -14,6 +14,20 @@ namespace qg {
 constexpr int kThreads = QG_THREADS;
 constexpr int kWarps = QG_THREADS / 32;
 
+// Base of the dynamic shared memory of every kernel here (all declarations
+// of an extern __shared__ array name the same block).
+extern __shared__ __align__(16) unsigned char qg_dyn_smem[];
+
+// p, a generic pointer into the dynamic shared memory, rebased on
+// qg_dyn_smem: the compiler then knows the address space and emits shared
+// loads and stores instead of generic ones.  The FFT buffers always live in
+// dynamic shared memory, but reach the transforms through structures whose
+// address space the compiler cannot see.
+template <typename T>
+__device__ __forceinline__ T* in_dyn_smem(T* p) {
+  return reinterpret_cast<T*>(qg_dyn_smem + (reinterpret_cast<unsigned char*>(p) - qg_dyn_smem));
+}
+
 template <typename R>
 struct Cx;
 template <>
@@ -212,7 +226,8 @@ __host__ __device__ inline int count_radix8(const int* radix, int npass) {
 // lanes of a warp) read consecutive entries.  The tables are read with
 // generic loads: they may sit in global or in shared memory.
 template <int RD, bool INV, typename C>
-__device__ __forceinline__ void fft_pass(C* buf, int n, int nb, int L, const C* __restrict__ twp) {
+__device__ __forceinline__ void fft_pass(C* gbuf, int n, int nb, int L, const C* __restrict__ twp) {
+  C* buf = in_dyn_smem(gbuf);
   const int lm = ilog2(L / RD);
   const int m = 1 << lm;
   const int lpv = ilog2(n / RD);
@@ -247,7 +262,8 @@ __device__ __forceinline__ void fft_pass(C* buf, int n, int nb, int L, const C* 
 // Last forward pass (block length RD, no twiddles), multiplication by i k / n
 // at the digit-reversed positions, first inverse pass -- all in registers.
 template <int RD, typename C, typename R>
-__device__ __forceinline__ void fft_center(C* buf, int n, int nb, const R* __restrict__ kd) {
+__device__ __forceinline__ void fft_center(C* gbuf, int n, int nb, const R* __restrict__ kd) {
+  C* buf = in_dyn_smem(gbuf);
   const int total = (nb * n) / RD;
   for (int b = threadIdx.x; b < total; b += kThreads) {
     const int e0 = b * RD;
@@ -269,8 +285,10 @@ __device__ __forceinline__ void fft_center(C* buf, int n, int nb, const R* __res
 
 // buf <- D buf for nb vectors (spectral first derivative, Sec. II D):
 // forward FFT, multiply by i k, inverse FFT (1/n folded into kd).
+// One out-of-line copy per precision: its call sites share the code (fewer
+// instruction-cache misses than an inlined copy at every site).
 template <typename R>
-__device__ __forceinline__ void spectral_derivative(typename Cx<R>::T* buf, int nb, const HOp<R>& H) {
+__device__ __noinline__ void spectral_derivative(typename Cx<R>::T* buf, int nb, const HOp<R>& H) {
   using C = typename Cx<R>::T;
   const int n = H.n, np = H.npass, n8 = H.n8;
   const C* tw = H.tw;
@@ -334,6 +352,7 @@ __device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T
   const R* F = H.F;
   const R* V = H.V;
   const int nb = (S <= nb_cap) ? S : 1;
+  sbuf = in_dyn_smem(sbuf);
   // U = (D + F) x
   for (int s0 = 0; s0 < S; s0 += nb) {
     for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[spad<C>(i)] = x[s0 * n + i];
@@ -380,6 +399,7 @@ __device__ __forceinline__ void apply_d_plus_f(const HOp<R>& H, typename Cx<R>::
   const int ln = ilog2(n);
   const R* F = H.F;
   const int nb = (S <= nb_cap) ? S : 1;
+  sbuf = in_dyn_smem(sbuf);
   for (int s0 = 0; s0 < S; s0 += nb) {
     for (int i = threadIdx.x; i < nb * n; i += kThreads) sbuf[spad<C>(i)] = x[s0 * n + i];
     __syncthreads();

@@ -147,7 +147,7 @@ struct Dom2D {
     const int n0 = this->n0, n1 = this->n1, N = this->N, S = this->S;
     const int r_lo = this->r_lo, r_hi = this->r_hi, c_lo = this->c_lo, c_hi = this->c_hi;
     const int cap_elems = this->cap_elems;
-    C* sb = reinterpret_cast<C*>(fb);
+    C* sb = in_dyn_smem(reinterpret_cast<C*>(fb));
     const HOp<R>* H = nullptr;
     C* U;
     C* T;
