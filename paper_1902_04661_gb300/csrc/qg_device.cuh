@@ -92,6 +92,14 @@ __host__ __device__ inline size_t padded_bytes(size_t elems, size_t elem_bytes) 
   const size_t e = elems + (elems >> (elem_bytes == 16 ? 3 : 4)) + 1;
   return ((e * elem_bytes) + 15) & ~size_t(15);
 }
+// Largest element count whose padded buffer fits in `bytes` (the inverse of
+// padded_bytes, exact).
+__host__ __device__ inline size_t padded_capacity(size_t bytes, size_t elem_bytes) {
+  size_t e = (bytes / elem_bytes) * 8 / 9;
+  while (e > 0 && padded_bytes(e, elem_bytes) > bytes) --e;
+  while (padded_bytes(e + 1, elem_bytes) <= bytes) ++e;
+  return e;
+}
 
 // ---------------------------------------------------------------------------
 // Deterministic CTA-wide sums of K values per thread.  The xor-butterfly

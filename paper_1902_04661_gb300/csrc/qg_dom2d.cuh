@@ -380,8 +380,9 @@ static __device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_
   }
   D.parity = 0;
   D.good = true;
-  // padded_bytes(e, 16) = 16 (e + e/8 + 1) rounded up: invert conservatively
-  D.cap_elems = (int)(((size_t)fft_bytes / 16 - 2) * 8 / 9);
+  // complex doubles (with padding) the FFT buffer holds; complex floats
+  // need less room for the same count
+  D.cap_elems = (int)padded_capacity((size_t)fft_bytes, 16);
   return D;
 }
 
