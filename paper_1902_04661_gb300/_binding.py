@@ -317,6 +317,10 @@ class State:
         _check(r, "qg_step_implicit", allow=(QG_ERR_NOT_CONVERGED,) if allow_fail else ())
         return st.as_dict()
 
+    def set_launch_width(self, ctas):
+        """2-D states: CTAs of the cooperative launch (0 = automatic)."""
+        _check(lib().qg_state_set_launch_width(self.handle, int(ctas)), "qg_state_set_launch_width")
+
     def autotune(self, method, order, scheme, dt, trial_steps=1, opts=None):
         """2-D states: pick the fastest cooperative launch width; returns the
         trial times (ms) at the automatic width, 1/2 and 1/4 of it."""
