@@ -72,7 +72,8 @@ static __device__ bool grid_barrier(unsigned* bar, int* err) {
 
 struct Dom2D {
   // H psi can form Re<x, y> and ||y||^2 in its last pass and reduce them
-  // across the grid in its closing barrier (see hpsi)
+  // across the grid in its closing barrier (see hpsi); the solvers use that
+  // for alpha and for residual norms
   static constexpr bool kFusedDots = true;
   const Inst2D* I;
   int len, N, n0, n1, S;

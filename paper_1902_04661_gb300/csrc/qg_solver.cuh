@@ -376,9 +376,10 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
       // Wn = H Vc - beta_k Vp ; alpha = <Vc, Wn> ; beta_{k+1} = ||Wn - alpha Vc||
       R alpha, betan;
       if constexpr (Dom::kFusedDots) {
-        // one grid-wide reduction per iteration, inside H psi:
-        // ||Wn - alpha Vc||^2 = ||Wn||^2 - alpha^2 (||Vc|| = 1, Vc _|_ Vp);
-        // Wn - alpha Vc is formed in the update pass below
+        // alpha is reduced inside H psi (its closing grid barrier).  beta is
+        // the norm of the formed vector Wn - alpha Vc, not ||Wn||^2 - alpha^2:
+        // that shortcut cancels, and the normalisation error it leaves in
+        // v_{k+1} grows from one iteration to the next on stiff problems.
         if (k == 1)
           D.template hpsi<R>(Vc, Wn, nullptr, (R)0, (R)0, cmk<C>((R)1, (R)0), sc);
         else
@@ -386,8 +387,14 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
         count_hpsi<R>(cnt);
         if (!D.ok()) return false;
         alpha = dv * sc[0];
-        const R w2 = dv * sc[1] - alpha * alpha;
-        betan = w2 > (R)0 ? sqrt(w2) : (R)0;
+        R wv[1] = {0};
+        D.each([&](int i) {
+          const C w = caxpy_r(-alpha, Vc[i], Wn[i]);
+          Wn[i] = w;
+          wv[0] = fma(w.x, w.x, fma(w.y, w.y, wv[0]));
+        });
+        if (!D.template sum<1>(wv, sc)) return false;
+        betan = sqrt(dv * sc[0]);
       } else {
         if (k == 1)
           D.template hpsi<R>(Vc, Wn, nullptr, (R)0, (R)0, cmk<C>((R)1, (R)0));
@@ -457,10 +464,7 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
         d = cmul(d, ir);
         Dq[i] = d;                                   // newest direction, in the oldest slot
         X[i] = caxpy(gk, d, X[i]);
-        if constexpr (Dom::kFusedDots)
-          Wn[i] = cscale(ibn, caxpy_r(-alpha, v, Wn[i]));   // v_{k+1} (alpha Vc removed here)
-        else
-          Wn[i] = cscale(ibn, Wn[i]);                       // v_{k+1}
+        Wn[i] = cscale(ibn, Wn[i]);                  // v_{k+1}
       });
       __syncthreads();
       C* t0 = Dq;
