@@ -92,6 +92,8 @@ struct Dom2D {
   int parity;
   bool good;
   int cap_elems;   // complex values one shared-memory FFT batch may hold
+  unsigned char* stage;   // shared copies of x and U for one batch (2 cap_elems
+                          // complex doubles), or null: read them from global
 
   // Every point of the owned rows, all surfaces.  Members are copied to
   // registers first (stores through generic pointers in f could alias *this).
@@ -149,6 +151,10 @@ struct Dom2D {
     const int r_lo = this->r_lo, r_hi = this->r_hi, c_lo = this->c_lo, c_hi = this->c_hi;
     const int cap_elems = this->cap_elems;
     C* sb = in_dyn_smem(reinterpret_cast<C*>(fb));
+    // staged batch: xs[e] = x and us[e] = U at the batch position e of the
+    // FFT buffer (no padding), so the pointwise loops read no global memory
+    C* xs = stage ? in_dyn_smem(reinterpret_cast<C*>(stage)) : nullptr;
+    C* us = xs ? xs + cap_elems : nullptr;
     const HOp<R>* H = nullptr;
     C* U;
     C* T;
@@ -182,7 +188,9 @@ struct Dom2D {
       for (int k = threadIdx.x; k < nv * n1; k += kThreads) {
         const int v = k / n1, j = k - v * n1;
         const int rl = v / S, s = v - rl * S;
-        sb[spad<C>(k)] = x[(size_t)s * N + (size_t)(r0 + rl) * n1 + j];
+        const C val = x[(size_t)s * N + (size_t)(r0 + rl) * n1 + j];
+        sb[spad<C>(k)] = val;
+        if (xs) xs[k] = val;
       }
       __syncthreads();
       if (nv > 0) spectral_derivative<R>(sb, nv, H1);
@@ -193,8 +201,12 @@ struct Dom2D {
           const int e = (rl * S + s) * n1 + j;
           C acc = sb[spad<C>(e)];
           for (int t = 0; t < S; ++t)
-            if (t != s) acc = caxpy_r(coupling2(F1, N, S, s, t, p), x[(size_t)t * N + p], acc);
-          U[(size_t)s * N + p] = acc;
+            if (t != s)
+              acc = caxpy_r(coupling2(F1, N, S, s, t, p), xs ? xs[(rl * S + t) * n1 + j] : x[(size_t)t * N + p], acc);
+          if (us)
+            us[e] = acc;
+          else
+            U[(size_t)s * N + p] = acc;
           sb[spad<C>(e)] = acc;
         }
       }
@@ -206,10 +218,11 @@ struct Dom2D {
         for (int s = 0; s < S; ++s) {
           C acc = sb[spad<C>((rl * S + s) * n1 + j)];
           for (int t = 0; t < S; ++t)
-            if (t != s) acc = caxpy_r(coupling2(F1, N, S, s, t, p), U[(size_t)t * N + p], acc);
-          const C xs = x[(size_t)s * N + p];
+            if (t != s)
+              acc = caxpy_r(coupling2(F1, N, S, s, t, p), us ? us[(rl * S + t) * n1 + j] : U[(size_t)t * N + p], acc);
+          const C xv = xs ? xs[(rl * S + s) * n1 + j] : x[(size_t)s * N + p];
           const R v = __ldg(V + (size_t)s * N + p);
-          T[(size_t)s * N + p] = cmk<C>(fma(mh, acc.x, v * xs.x), fma(mh, acc.y, v * xs.y));
+          T[(size_t)s * N + p] = cmk<C>(fma(mh, acc.x, v * xv.x), fma(mh, acc.y, v * xv.y));
         }
       }
       __syncthreads();
@@ -230,7 +243,9 @@ struct Dom2D {
       for (int k = threadIdx.x; k < nv * n0; k += kThreads) {
         const int v = k / n0, i = k - v * n0;
         const int cl = v / S, s = v - cl * S;
-        sb[spad<C>(k)] = x[(size_t)s * N + (size_t)i * n1 + (c0 + cl)];
+        const C val = x[(size_t)s * N + (size_t)i * n1 + (c0 + cl)];
+        sb[spad<C>(k)] = val;
+        if (xs) xs[k] = val;
       }
       __syncthreads();
       if (nv > 0) spectral_derivative<R>(sb, nv, H0);
@@ -241,8 +256,12 @@ struct Dom2D {
           const int e = (cl * S + s) * n0 + i;
           C acc = sb[spad<C>(e)];
           for (int t = 0; t < S; ++t)
-            if (t != s) acc = caxpy_r(coupling2(F0, N, S, s, t, p), x[(size_t)t * N + p], acc);
-          U[(size_t)s * N + p] = acc;
+            if (t != s)
+              acc = caxpy_r(coupling2(F0, N, S, s, t, p), xs ? xs[(cl * S + t) * n0 + i] : x[(size_t)t * N + p], acc);
+          if (us)
+            us[e] = acc;
+          else
+            U[(size_t)s * N + p] = acc;
           sb[spad<C>(e)] = acc;
         }
       }
@@ -254,15 +273,16 @@ struct Dom2D {
         for (int s = 0; s < S; ++s) {
           C acc = sb[spad<C>((cl * S + s) * n0 + i)];
           for (int t = 0; t < S; ++t)
-            if (t != s) acc = caxpy_r(coupling2(F0, N, S, s, t, p), U[(size_t)t * N + p], acc);
+            if (t != s)
+              acc = caxpy_r(coupling2(F0, N, S, s, t, p), us ? us[(cl * S + t) * n0 + i] : U[(size_t)t * N + p], acc);
           const C tt = T[(size_t)s * N + p];
           const C hx = cmk<C>(fma(mh, acc.x, tt.x), fma(mh, acc.y, tt.y));
-          const C xs = x[(size_t)s * N + p];
-          C out = caxpy(c, hx, cmk<C>(a * xs.x, a * xs.y));
+          const C xv = xs ? xs[(cl * S + s) * n0 + i] : x[(size_t)s * N + p];
+          C out = caxpy(c, hx, cmk<C>(a * xv.x, a * xv.y));
           if (e != (R)0) out = caxpy_r(e, z[(size_t)s * N + p], out);
           y[(size_t)s * N + p] = out;
           if (dots) {
-            pd[0] = fma(xs.x, out.x, fma(xs.y, out.y, pd[0]));
+            pd[0] = fma(xv.x, out.x, fma(xv.y, out.y, pd[0]));
             pd[1] = fma(out.x, out.x, fma(out.y, out.y, pd[1]));
           }
         }
@@ -305,7 +325,7 @@ __host__ __device__ inline size_t tables2d_bytes(int n0, int n1) {
 // tab_off > 0: the tables are copied to dyn + tab_off (16-byte aligned) and
 // the transforms read them from there.
 static __device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_bytes, double* red,
-                                   int tab_off = 0) {
+                                   int tab_off = 0, int stage_bytes = 0) {
   Dom2D D;
   D.I = &I;
   D.n0 = I.n[0];
@@ -321,7 +341,8 @@ static __device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_
   D.c_hi = min(D.n1, D.c_lo + cp);
   D.dv = I.dv;
   D.fb = dyn;
-  D.gm = dyn + fft_bytes;
+  D.stage = stage_bytes > 0 ? dyn + fft_bytes : nullptr;
+  D.gm = dyn + fft_bytes + stage_bytes;
   D.red = red;
   for (int d = 0; d < 2; ++d) {
     D.H64[d].n = I.n[d];

@@ -9,12 +9,12 @@
 namespace qg {
 
 // out = H psi (c = 1) or <psi|H|psi> (energy != null).
-__global__ void __launch_bounds__(QG_THREADS, 1) apply_h2d_kernel(const Inst2D I, int fft_bytes, int tab_off,
-                                                                  double2* out, double* energy) {
+__global__ void __launch_bounds__(QG_THREADS, 1) apply_h2d_kernel(const Inst2D I, int fft_bytes, int stage_bytes,
+                                                                  int tab_off, double2* out, double* energy) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ double red[kWarps * 16];
   __shared__ double sc[64];
-  Dom2D D = make_dom2d(I, dyn, fft_bytes, red, tab_off);
+  Dom2D D = make_dom2d(I, dyn, fft_bytes, red, tab_off, stage_bytes);
   D.hpsi<double>(I.psi, out, nullptr, 0.0, 0.0, make_double2(1.0, 0.0));
   if (energy) {
     double v[2] = {0.0, 0.0};
@@ -145,17 +145,25 @@ static size_t with_tables(const Inst2D& I, size_t smem, int* tab_off) {
   return off + tab;
 }
 
+// Shared copies of x and U for one FFT batch (two arrays of the batch's
+// complex-double capacity) when they fit beside the batch within 160 KB.
+static int stage2d_bytes(int fft_bytes) {
+  const size_t st = 2 * 16 * qg::padded_capacity((size_t)fft_bytes, 16);
+  return (size_t)fft_bytes + st <= (size_t)160 * 1024 ? (int)st : 0;
+}
+
 cudaError_t qg_launch_propagate2d(const Inst2D& I, const StepPlan& P, qg_step_stats* d_stats, cudaStream_t st) {
   const int G = qg_grid2d_ctas(I);
   int fft = (int)fft2d_bytes(I);
+  int stage = stage2d_bytes(fft);
   int tab_off = 0;
-  const size_t smem = with_tables(I, fft + qg::gmres_smem_bytes(P.restart), &tab_off);
+  const size_t smem = with_tables(I, fft + stage + qg::gmres_smem_bytes(P.restart), &tab_off);
   cudaError_t e = cudaMemsetAsync(I.bar, 0, 2 * sizeof(unsigned), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.err, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   Inst2D Ic = I;
   StepPlan Pc = P;
-  void* args[] = {&Ic, &Pc, &fft, &tab_off, &d_stats};
+  void* args[] = {&Ic, &Pc, &fft, &stage, &tab_off, &d_stats};
   const void* fn = I.precision == QG_C64_MIXED ? qg_propagate2d_fn<1>() : qg_propagate2d_fn<0>();
   return coop_launch(fn, G, smem, args, st);
 }
@@ -163,13 +171,14 @@ cudaError_t qg_launch_propagate2d(const Inst2D& I, const StepPlan& P, qg_step_st
 cudaError_t qg_launch_apply_h2d(const Inst2D& I, double2* d_out, double* d_energy, cudaStream_t st) {
   const int G = qg_grid2d_ctas(I);
   int fft = (int)fft2d_bytes(I);
+  int stage = stage2d_bytes(fft);
   int tab_off = 0;
-  const size_t smem = with_tables(I, fft + qg::gmres_smem_bytes(1), &tab_off);
+  const size_t smem = with_tables(I, fft + stage + qg::gmres_smem_bytes(1), &tab_off);
   cudaError_t e = cudaMemsetAsync(I.bar, 0, 2 * sizeof(unsigned), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(I.err, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   Inst2D Ic = I;
-  void* args[] = {&Ic, &fft, &tab_off, &d_out, &d_energy};
+  void* args[] = {&Ic, &fft, &stage, &tab_off, &d_out, &d_energy};
   return coop_launch((const void*)qg::apply_h2d_kernel, G, smem, args, st);
 }
 

@@ -13,11 +13,12 @@ namespace qg {
 
 template <int MODE>
 __global__ void __launch_bounds__(QG_THREADS, 1)
-    propagate2d_kernel(const Inst2D I, const StepPlan P, int fft_bytes, int tab_off, qg_step_stats* st) {
+    propagate2d_kernel(const Inst2D I, const StepPlan P, int fft_bytes, int stage_bytes, int tab_off,
+                       qg_step_stats* st) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ double red[kWarps * 16];
   __shared__ double sc[64];
-  Dom2D D = make_dom2d(I, dyn, fft_bytes, red, tab_off);
+  Dom2D D = make_dom2d(I, dyn, fft_bytes, red, tab_off, stage_bytes);
   const size_t len = D.len;
   Counters cnt{0, 0, 0, 0, 0, 0, 0, 0, 0.0};
   long long nsub = 0;
