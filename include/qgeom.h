@@ -101,7 +101,8 @@ typedef struct qg_batch* qg_batch_t;
  * true_residual: 1 = recompute ||b - A x|| after convergence and restart if
  *      it exceeds tol (one more H psi per solve); default 0.
  * inner_tol: QG_C64_MIXED only -- relative tolerance of each complex64 inner
- *      solve, default 1e-6.
+ *      solve, default 1e-6; a refinement step whose residual rho is already
+ *      close to the target uses max(inner_tol, tol ||b|| / (4 rho)).
  * max_outer: QG_C64_MIXED only -- cap on FP64 refinement steps per implicit
  *      solve, default 10; exceeding it is QG_ERR_NOT_CONVERGED.
  * solver: QG_SOLVER_GMRES (default; restarted GMRES with Arnoldi/CGS as in

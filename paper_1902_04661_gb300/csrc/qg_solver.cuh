@@ -578,6 +578,10 @@ __device__ bool solve_mixed(Dom& D, const StepPlan& P, double tau, const double2
     }
     if (outer == P.max_outer) break;
     cnt.outer++;
+    // the inner solve need not reduce the residual further than the outer
+    // target asks (with a factor 4 in hand): the last refinement step is
+    // usually looser than inner_tol
+    sp.tol = fmax(P.inner_tol, 0.25 * target / rho);
     const double ir = 1.0 / rho;
     D.each([&](int i) {
       const double2 v = Rv[i];
