@@ -1,9 +1,9 @@
 // Implicit solves, composed steps and the adjoint sweep, written once over a
 // "domain" that says which elements a thread owns, how a sum over the whole
 // state is formed and how H psi is applied:
-//   Dom1D -- one CTA owns one whole 1-D instance (qg_kernels.cu);
+//   Dom1D -- one CTA owns one whole 1-D instance (qg_dom1d.cuh);
 //   Dom2D -- all CTAs of a cooperative launch share one 2-D instance
-//            (qg_kernels2d.cu).
+//            (qg_dom2d.cuh).
 // A domain D provides
 //   D.len                                  elements of one state vector
 //   D.each(f)                              f(i) for every owned element i
@@ -13,7 +13,10 @@
 //   D.template hpsi<R>(x, y, z, e, a, c)   y = e z + a x + c (H x), precision R
 //   D.dv                                   volume element of the inner product
 //   D.ok()                                 false after a failed grid barrier
-//   D.fail()                               forces ok() false (error exit)
+//   Dom::kFusedDots                        true if D.template hpsi<R>(x, y, z,
+//                                          e, a, c, dots) also returns
+//                                          Re<x, y> and ||y||^2 (raw sums) in
+//                                          dots[0..1], reduced with H psi
 // plus the smem GMRES arrays D.gm, and the workspace vectors.
 #pragma once
 
