@@ -141,7 +141,7 @@ def fp64_peak_tflops(sm_mhz=None):
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum).
 # Reported only for that configuration; it must be re-measured whenever the
 # kernel changes.
-NCU_TRAFFIC_BYTES = 2.529321e9 + 14.909761e9
+NCU_TRAFFIC_BYTES = None
 
 
 def _traffic(args, B):
@@ -151,13 +151,9 @@ def _traffic(args, B):
 
 
 def _guess(args):
-    """Start of each implicit solve: 0 = explicit Euler (Sec. II B), 1 = zero.
-    Default: the paper's Euler start, except for the 2-D workload, where the
-    zero start saves the mixed form one FP64 residual per solve (both arms of
-    that comparison use the same start and the same tolerance)."""
-    g = getattr(args, "guess", None)
-    if g is None:
-        g = "zero" if getattr(args, "workload", "nai") == "2d" else "euler"
+    """Start of each implicit solve: 0 = explicit Euler (Sec. II B, the
+    default), 1 = zero."""
+    g = getattr(args, "guess", None) or "euler"
     return 1 if g == "zero" else 0
 
 
@@ -718,8 +714,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--guess", default=None, choices=["euler", "zero"],
-                    help="start of each implicit solve: explicit Euler (Sec. II B; default) or zero "
-                         "(default for --workload 2d)")
+                    help="start of each implicit solve: explicit Euler (Sec. II B; default) or zero")
     ap.add_argument("--sweep", action="store_true", help="convergence-error sweep that fixes the operating point")
     ap.add_argument("--solver", default="lanczos", choices=["gmres", "lanczos"],
                     help="Krylov method of the implicit steps (same minimal-residual iterates)")

@@ -657,22 +657,24 @@ __device__ __forceinline__ void write_stats(qg_step_stats* st, const Counters& c
 // minimal-residual iterate from zero after k + 2 iterations minimises over
 // K_{k+2}(H, b), which contains every point the Euler guess reaches after k
 // iterations for the same k + 2 H psi evaluations.
+// guess_ready: X already holds the explicit-Euler start (formed by the caller
+// without an H psi evaluation).
 template <int MODE, class Dom>
 __device__ __forceinline__ bool implicit_solve(Dom& D, const StepPlan& P, double tau, const double2* b, double2* X,
-                                               bool mixed, Counters& cnt, double* sc) {
-  const int zero = P.guess == QG_GUESS_ZERO;
+                                               bool mixed, Counters& cnt, double* sc, bool guess_ready = false) {
+  const int zero = !guess_ready && P.guess == QG_GUESS_ZERO;
   if (zero) {
     D.each([&](int i) { X[i] = make_double2(0.0, 0.0); });
     __syncthreads();
   }
   if constexpr (MODE != 0) {
     if (MODE == 1 || mixed) {
-      if (!zero) guess_mixed(D, tau, b, X, cnt);
+      if (!zero && !guess_ready) guess_mixed(D, tau, b, X, cnt);
       return solve_mixed(D, P, tau, b, X, cnt, sc, zero);
     }
   }
   if constexpr (MODE != 1) {
-    if (!zero) {
+    if (!zero && !guess_ready) {
       D.template hpsi<double>(b, X, nullptr, 0.0, 1.0, make_double2(0.0, -tau));
       cnt.hpsi += 1;
     }
@@ -687,6 +689,9 @@ __device__ long long run_steps(Dom& D, const StepPlan& P, double2* psi, double2*
                                long long& nsub, double* sc) {
   const int len = D.len;
   long long failed = -1;
+  // midpoint with the explicit-Euler start and psi' = 2 chi - psi: carry
+  // H psi from one sub-step to the next in B (unused by the midpoint rule)
+  const bool recycle = P.method != QG_TRAPEZOIDAL && P.guess == QG_GUESS_EULER && !P.mid_epi;
   dcopy(D, P0, psi);
   for (long long step = 0; step < P.nsteps && failed < 0; ++step) {
     if (P.run == QG_RUN_CHECKPOINT && ckpt && step % every == 0 && step / every < nckpt)
@@ -704,14 +709,38 @@ __device__ long long run_steps(Dom& D, const StepPlan& P, double2* psi, double2*
       } else {
         // guess chi0 = (1 - i tau H) psi ; solve (1 + i tau H) chi = psi ;
         // psi' = (1 - i tau H) chi  (or 2 chi - psi)
-        ok = implicit_solve<MODE>(D, P, tau, psi, X, mixed, cnt, sc);
+        if (recycle) {
+          // B carries H psi: exact at the first fraction of each composed
+          // step, then by the recurrence below, so the explicit-Euler start
+          // costs no H psi (the solve still forms its true residual)
+          if (f == 0) {
+            D.template hpsi<double>(psi, B, nullptr, 0.0, 0.0, make_double2(1.0, 0.0));
+            cnt.hpsi += 1;
+          }
+          D.each([&](int i) {
+            const double2 p = psi[i], h = B[i];
+            X[i] = make_double2(fma(tau, h.y, p.x), fma(-tau, h.x, p.y));
+          });
+          __syncthreads();
+          ok = implicit_solve<MODE>(D, P, tau, psi, X, mixed, cnt, sc, true);
+        } else {
+          ok = implicit_solve<MODE>(D, P, tau, psi, X, mixed, cnt, sc);
+        }
         if (ok) {
           if (P.mid_epi) {
             D.template hpsi<double>(X, psi, nullptr, 0.0, 1.0, mic);
             cnt.hpsi += 1;
           } else {
+            // psi' = 2 chi - psi and, when recycling, H psi' = 2 H chi - H psi
+            // with H chi = i (chi - psi) / tau from (1 + i tau H) chi = psi
+            const double it = 1.0 / tau;
             D.each([&](int i) {
               const double2 c = X[i], p = psi[i];
+              if (recycle) {
+                const double2 h = B[i];
+                const double dx = (c.x - p.x) * it, dy = (c.y - p.y) * it;
+                B[i] = make_double2(-2.0 * dy - h.x, 2.0 * dx - h.y);
+              }
               psi[i] = make_double2(2.0 * c.x - p.x, 2.0 * c.y - p.y);
             });
             __syncthreads();

@@ -18,12 +18,11 @@ def _args(**kw):
     return argparse.Namespace(**base)
 
 
-def test_default_start_is_euler_except_2d():
+def test_default_start_is_euler():
     assert bench._guess(_args()) == 0 and bench._guess_name(_args()) == "euler"
-    assert bench._guess(_args(workload="2d")) == 1
+    assert bench._guess(_args(workload="2d")) == 0
     assert bench._guess(_args(workload="batched")) == 0
-    assert bench._guess(_args(guess="zero")) == 1
-    assert bench._guess(_args(workload="2d", guess="euler")) == 0
+    assert bench._guess(_args(guess="zero")) == 1 and bench._guess_name(_args(guess="zero")) == "zero"
 
 
 def test_traffic_only_for_the_measured_configuration():

@@ -42,4 +42,5 @@ def test_lanczos_equals_gmres_full_size(qglib, cuda):
     print("lanczos vs gmres N=2048 Suzuki-6: %.2e; krylov/substep %.2f vs %.2f" %
           (err, lb["n_krylov"] / lb["n_substeps"], ga["n_krylov"] / ga["n_substeps"]))
     assert err < 1e-11
-    assert lb["n_hpsi"] == 2 * lb["n_substeps"] + lb["n_krylov"] + lb["n_restart"]
+    # one exact H psi per composed step (3), then 1 + I per sub-step
+    assert lb["n_hpsi"] == 3 + lb["n_substeps"] + lb["n_krylov"] + lb["n_restart"]
