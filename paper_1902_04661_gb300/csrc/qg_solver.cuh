@@ -534,9 +534,13 @@ __device__ bool solve_fp64(Dom& D, const StepPlan& P, double tau, const double2*
 // Mixed-precision implicit solve: FP64 residual r = b - (1 + i tau H) X,
 // complex64 GMRES for (1 + i tau H) d = r / ||r|| to inner_tol, X += ||r|| d,
 // until ||r|| <= tol ||b||.
+//
+// r0_ready: D.res64 already holds an estimate of b - (1 + i tau H) X (from
+// carried H^2 psi, see run_steps).  It only seeds the first inner solve: the
+// refinement stops on exactly computed FP64 residuals only.
 template <class Dom>
 __device__ bool solve_mixed(Dom& D, const StepPlan& P, double tau, const double2* b, double2* X, Counters& cnt,
-                            double* sc, int x0_zero = 0) {
+                            double* sc, int x0_zero = 0, bool r0_ready = false) {
   double2* Rv = D.res64;
   float2* r32 = D.r32;
   float2* d32 = D.d32;
@@ -554,10 +558,19 @@ __device__ bool solve_mixed(Dom& D, const StepPlan& P, double tau, const double2
   SolveParams sp{P.inner_tol, P.restart, P.max_iters, P.reorth, 0, P.solver, 1};
   for (int outer = 0; outer <= P.max_outer; ++outer) {
     double rho;
+    const bool estimate = outer == 0 && r0_ready && !x0_zero;
     if (outer == 0 && x0_zero) {
       D.each([&](int i) { Rv[i] = b[i]; });
       __syncthreads();
       rho = bn;
+    } else if (estimate) {
+      double rv[1] = {0.0};
+      D.each([&](int i) {
+        const double2 a = Rv[i];
+        rv[0] = fma(a.x, a.x, fma(a.y, a.y, rv[0]));
+      });
+      if (!D.template sum<1>(rv, sc)) return false;
+      rho = sqrt(dv * sc[0]);
     } else if constexpr (Dom::kFusedDots) {
       D.template hpsi<double>(X, Rv, b, 1.0, -1.0, mic, sc);
       cnt.hpsi++;
@@ -574,12 +587,13 @@ __device__ bool solve_mixed(Dom& D, const StepPlan& P, double tau, const double2
       if (!D.template sum<1>(rv, sc)) return false;
       rho = sqrt(dv * sc[0]);
     }
-    if (rho <= target || bn == 0.0) {
+    if (!estimate && (rho <= target || bn == 0.0)) {
       const double r = bn > 0.0 ? rho / bn : 0.0;
       if (r > cnt.max_res) cnt.max_res = r;
       return true;
     }
     if (outer == P.max_outer) break;
+    if (estimate && rho == 0.0) continue;   // nothing to refine: check exactly
     cnt.outer++;
     // the inner solve need not reduce the residual further than the outer
     // target asks (with a factor 4 in hand): the last refinement step is
@@ -661,7 +675,8 @@ __device__ __forceinline__ void write_stats(qg_step_stats* st, const Counters& c
 // without an H psi evaluation).
 template <int MODE, class Dom>
 __device__ __forceinline__ bool implicit_solve(Dom& D, const StepPlan& P, double tau, const double2* b, double2* X,
-                                               bool mixed, Counters& cnt, double* sc, bool guess_ready = false) {
+                                               bool mixed, Counters& cnt, double* sc, bool guess_ready = false,
+                                               bool r0_ready = false) {
   const int zero = !guess_ready && P.guess == QG_GUESS_ZERO;
   if (zero) {
     D.each([&](int i) { X[i] = make_double2(0.0, 0.0); });
@@ -670,7 +685,7 @@ __device__ __forceinline__ bool implicit_solve(Dom& D, const StepPlan& P, double
   if constexpr (MODE != 0) {
     if (MODE == 1 || mixed) {
       if (!zero && !guess_ready) guess_mixed(D, tau, b, X, cnt);
-      return solve_mixed(D, P, tau, b, X, cnt, sc, zero);
+      return solve_mixed(D, P, tau, b, X, cnt, sc, zero, r0_ready);
     }
   }
   if constexpr (MODE != 1) {
@@ -692,6 +707,12 @@ __device__ long long run_steps(Dom& D, const StepPlan& P, double2* psi, double2*
   // midpoint with the explicit-Euler start and psi' = 2 chi - psi: carry
   // H psi from one sub-step to the next in B (unused by the midpoint rule)
   const bool recycle = P.method != QG_TRAPEZOIDAL && P.guess == QG_GUESS_EULER && !P.mid_epi;
+  // the mixed form also carries H^2 psi (in the FP64 basis slot after its
+  // residual, unused by that form): the residual of the Euler start is then
+  // -tau^2 H^2 psi, and its first FP64 residual costs no H psi
+  bool carry2 = false;
+  if constexpr (MODE != 0) carry2 = recycle && (MODE == 1 || mixed);
+  double2* H2 = D.res64 + len;
   dcopy(D, P0, psi);
   for (long long step = 0; step < P.nsteps && failed < 0; ++step) {
     if (P.run == QG_RUN_CHECKPOINT && ckpt && step % every == 0 && step / every < nckpt)
@@ -716,13 +737,23 @@ __device__ long long run_steps(Dom& D, const StepPlan& P, double2* psi, double2*
           if (f == 0) {
             D.template hpsi<double>(psi, B, nullptr, 0.0, 0.0, make_double2(1.0, 0.0));
             cnt.hpsi += 1;
+            if (carry2) {
+              D.template hpsi<double>(B, H2, nullptr, 0.0, 0.0, make_double2(1.0, 0.0));
+              cnt.hpsi += 1;
+            }
           }
+          const double t2 = tau * tau;
+          double2* Rv = D.res64;
           D.each([&](int i) {
             const double2 p = psi[i], h = B[i];
             X[i] = make_double2(fma(tau, h.y, p.x), fma(-tau, h.x, p.y));
+            if (carry2) {
+              const double2 g = H2[i];
+              Rv[i] = make_double2(-t2 * g.x, -t2 * g.y);   // psi - (1 + i tau H) X
+            }
           });
           __syncthreads();
-          ok = implicit_solve<MODE>(D, P, tau, psi, X, mixed, cnt, sc, true);
+          ok = implicit_solve<MODE>(D, P, tau, psi, X, mixed, cnt, sc, true, carry2);
         } else {
           ok = implicit_solve<MODE>(D, P, tau, psi, X, mixed, cnt, sc);
         }
@@ -739,7 +770,14 @@ __device__ long long run_steps(Dom& D, const StepPlan& P, double2* psi, double2*
               if (recycle) {
                 const double2 h = B[i];
                 const double dx = (c.x - p.x) * it, dy = (c.y - p.y) * it;
-                B[i] = make_double2(-2.0 * dy - h.x, 2.0 * dx - h.y);
+                const double2 hc = make_double2(-dy, dx);               // H chi
+                B[i] = make_double2(2.0 * hc.x - h.x, 2.0 * hc.y - h.y);
+                if (carry2) {
+                  // H^2 chi = i (H chi - H psi) / tau ; H^2 psi' = 2 H^2 chi - H^2 psi
+                  const double2 g = H2[i];
+                  const double ex = (hc.x - h.x) * it, ey = (hc.y - h.y) * it;
+                  H2[i] = make_double2(-2.0 * ey - g.x, 2.0 * ex - g.y);
+                }
               }
               psi[i] = make_double2(2.0 * c.x - p.x, 2.0 * c.y - p.y);
             });
