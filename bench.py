@@ -141,7 +141,7 @@ def fp64_peak_tflops(sm_mhz=None):
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum).
 # Reported only for that configuration; it must be re-measured whenever the
 # kernel changes.
-NCU_TRAFFIC_BYTES = None
+NCU_TRAFFIC_BYTES = 5.079719e9 + 18.604768e9
 
 
 def _traffic(args, B):
