@@ -213,7 +213,13 @@ qg_status qg_apply_h(qg_state_t s, void* out, int on_device);
 
 /* One composed time step dt (Secs. II B, II C): method QG_TRAPEZOIDAL or
  * QG_MIDPOINT, order 2/4/6/8, scheme QG_TRIPLE_JUMP or QG_SUZUKI.  opts may
- * be NULL (defaults); stats may be NULL. */
+ * be NULL (defaults); stats may be NULL.
+ * Cost in H psi per elementary step (Table I counts 3 + I, I Krylov
+ * iterations): trapezoidal 3 + I; midpoint with psi' = 2 chi - psi and the
+ * explicit-Euler start 1 + I, plus one exact H psi per composed step, since
+ * H psi' = 2 H chi - H psi with H chi = i (chi - psi) / tau is carried from
+ * one elementary step to the next (QG_C64_MIXED also carries H^2 psi: two
+ * FP64 H psi per elementary step). */
 qg_status qg_step_implicit(qg_state_t s, int method, int order, int scheme, double dt,
                            const qg_solver_opts* opts, qg_step_stats* stats);
 /* nsteps composed steps in one device launch. */
