@@ -2,6 +2,7 @@
 
 U_expl(e)  = 1 - i e H / hbar                           Eq. (exp_euler)
 U_impl(e)  = (1 + i e H / hbar)^{-1}                    Eq. (imp_euler)
+SOD        psi(t+e) = psi(t-e) - 2 i e H psi(t) / hbar  Eq. (sod_method)
 U_trap(dt) = U_impl(dt/2) U_expl(dt/2)                  Eq. (trap_rule)
 U_midp(dt) = U_expl(dt/2) U_impl(dt/2)                  Eq. (imp_midpoint)
 composed   = product over the flat schedule of composition.schedule().
@@ -19,6 +20,9 @@ from . import composition
 HBAR = 1.0
 TRAPEZOIDAL = 0
 MIDPOINT = 1
+EXPLICIT_EULER = 2
+IMPLICIT_EULER = 3
+SOD = 4
 
 
 class DenseStepper:
@@ -31,13 +35,16 @@ class DenseStepper:
         v = psi.reshape(-1)
         return (v - 1j * eps / HBAR * (self.H @ v)).reshape(psi.shape)
 
-    def impl(self, psi, eps):
+    def _solve(self, rhs, eps):
+        """(1 + i eps H / hbar)^{-1} rhs; rhs a vector or an (n, k) matrix."""
         key = float(eps)
         if key not in self._lu:
             A = np.eye(self.n, dtype=np.complex128) + 1j * eps / HBAR * self.H
             self._lu[key] = sla.lu_factor(A, check_finite=False)
-        x = sla.lu_solve(self._lu[key], psi.reshape(-1), check_finite=False)
-        return x.reshape(psi.shape)
+        return sla.lu_solve(self._lu[key], rhs, check_finite=False)
+
+    def impl(self, psi, eps):
+        return self._solve(psi.reshape(-1), eps).reshape(psi.shape)
 
     def trap(self, psi, dt):
         return self.impl(self.expl(psi, dt / 2), dt / 2)
@@ -61,6 +68,62 @@ class DenseStepper:
         for _ in range(nsteps):
             psi = self.composed(psi, dt, method, order, scheme)
         return psi
+
+    def propagate_columns(self, states, dt, nsteps, method, order=2, scheme=composition.SUZUKI):
+        """The same composed steps applied to several states at once: states
+        is a sequence of k states (or an (k, ...) array); every implicit
+        Euler factor is one LU solve with k right-hand sides.  Returns an
+        array of the k propagated states."""
+        states = np.asarray(states, dtype=np.complex128)
+        shape = states.shape
+        P = states.reshape(shape[0], self.n).T.copy()
+        fr = composition.schedule(order, scheme)
+        for _ in range(nsteps):
+            for f in fr:
+                eps = f * dt / 2
+                if method == TRAPEZOIDAL:
+                    P = self._solve(P - 1j * eps / HBAR * (self.H @ P), eps)
+                elif method == MIDPOINT:
+                    X = self._solve(P, eps)
+                    P = X - 1j * eps / HBAR * (self.H @ X)
+                else:
+                    raise ValueError("unknown method %r" % (method,))
+        return P.T.reshape(shape)
+
+
+    def euler_steps(self, psi, eps, nsteps, method):
+        """nsteps explicit (Eq. exp_euler) or implicit (Eq. imp_euler) Euler
+        steps of size eps: first order, neither unitary nor symmetric."""
+        for _ in range(nsteps):
+            if method == EXPLICIT_EULER:
+                psi = self.expl(psi, eps)
+            elif method == IMPLICIT_EULER:
+                psi = self.impl(psi, eps)
+            else:
+                raise ValueError("unknown Euler method %r" % (method,))
+        return psi
+
+    def rk2(self, psi, h):
+        """One two-stage Runge-Kutta step of size h (h < 0 steps backward) of
+        d psi/dt = -(i/hbar) H psi: k1 = f(psi), k2 = f(psi + h k1 / 2),
+        psi + h k2."""
+        v = psi.reshape(-1)
+        k1 = -1j / HBAR * (self.H @ v)
+        k2 = -1j / HBAR * (self.H @ (v + 0.5 * h * k1))
+        return (v + h * k2).reshape(psi.shape)
+
+    def sod(self, psi, eps, nsteps, psi_prev=None):
+        """Second-order differencing, Eq. (sod_method):
+        psi(t + eps) = psi(t - eps) - 2 (i/hbar) eps H psi(t).
+        The missing psi(-eps) is approximated by one two-stage Runge-Kutta
+        step backward from psi(0) (Sec. III), unless given.  Returns
+        (psi(n eps), psi((n - 1) eps))."""
+        prev = self.rk2(psi, -eps) if psi_prev is None else psi_prev
+        cur = psi
+        for _ in range(nsteps):
+            nxt = (prev.reshape(-1) - 2j * eps / HBAR * (self.H @ cur.reshape(-1))).reshape(psi.shape)
+            prev, cur = cur, nxt
+        return cur, prev
 
 
 def exact(H, psi, t):

@@ -75,3 +75,63 @@ def test_implicit_euler_taylor_expansion():
     coef = np.linalg.lstsq(np.vander(eps, 6, increasing=True), u, rcond=None)[0]
     want = [complex(a, b) for a, b in g["coefficients_of_epsH_powers"]]
     np.testing.assert_allclose(coef[:4], want, atol=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# "Optimal" compositions (Sec. II C) and the free-algebra order conditions
+
+
+@pytest.mark.parametrize("scheme", [comp.TRIPLE_JUMP, comp.SUZUKI])
+@pytest.mark.parametrize("order", [4, 6, 8])
+def test_recursive_schemes_meet_the_general_order_conditions(scheme, order):
+    g = comp.schedule(order, scheme)
+    scale = sum(abs(x) for x in g) ** order
+    assert comp.order_condition_residual(g, order) < 1e-14 * scale
+    if order < 8:
+        assert comp.order_condition_residual(g, order + 2) > 1e-6
+
+
+@pytest.mark.parametrize("order,M,gmax", [(6, 9, 0.7985439909348300), (8, 17, 0.6055085338300345)])
+def test_kahan_li_coefficients(order, M, gmax):
+    g = comp.schedule(order, comp.OPTIMAL)
+    assert len(g) == M
+    assert abs(sum(g) - 1.0) < 1e-15
+    assert g == g[::-1]
+    assert abs(max(abs(x) for x in g) - gmax) < 1e-15
+    # order exactly `order`: every condition up to that degree, not the next
+    assert comp.order_condition_residual(g, order) < 1e-15
+    assert comp.order_condition_residual(g, order + 2) > 1e-5
+    # a wrong digit anywhere breaks the conditions
+    for i in range(M // 2 + 1):
+        bad = list(g)
+        bad[i] += 1e-9
+        bad[M - 1 - i] = bad[i]
+        assert comp.order_condition_residual(bad, order) > 1e-10
+
+
+def test_scalar_conditions_alone_do_not_pass_the_general_check():
+    # a palindrome of M = 9 with sum 1, sum gamma^3 = sum gamma^5 = 0 meets the
+    # scalar (commuting) conditions of order 6 but not the non-commutative one
+    # at degree 5: the free-algebra check must see the difference
+    from scipy.optimize import fsolve
+    fixed = [0.3, 0.25]
+
+    def eqs(v):
+        g = comp.palindrome(fixed + list(v))
+        return [sum(g) - 1.0, sum(x ** 3 for x in g), sum(x ** 5 for x in g)]
+
+    v = fsolve(eqs, [-0.6, 0.1, 0.9], xtol=1e-13)
+    g = comp.palindrome(fixed + list(v))
+    assert max(abs(e) for e in eqs(v)) < 1e-13
+    assert comp.order_condition_residual(g, 6) > 1e-4
+
+
+@pytest.mark.parametrize("order", [6, 8])
+def test_scalar_optimal_cayley_has_the_order(order):
+    f = comp.schedule(order, comp.OPTIMAL)
+    xs = np.geomspace(1e-3, 6.0, 160)
+    err = np.array([abs(_scalar(f, x) - np.exp(-1j * x)) for x in xs])
+    sel = (err > 1e-12) & (err < 1e-7)
+    assert sel.sum() >= 5
+    slope = np.polyfit(np.log(xs[sel]), np.log(err[sel]), 1)[0]
+    assert abs(slope - (order + 1)) < 0.3

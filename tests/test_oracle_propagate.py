@@ -86,3 +86,14 @@ def test_global_error_order_against_exact_evolution(order, scheme, ns):
         err.append(np.linalg.norm(st.propagate(psi, t / n, n, prop.MIDPOINT, order, scheme) - ex))
     slope = np.log(err[0] / err[1]) / np.log(2.0)
     assert abs(slope - order) < 0.35, (err, slope)
+
+
+@pytest.mark.parametrize("method", [prop.TRAPEZOIDAL, prop.MIDPOINT])
+def test_columns_route_equals_one_state_route(small, method):
+    # several states through one LU solve with many right-hand sides give
+    # the states propagated one by one
+    st = prop.DenseStepper(small["H"])
+    many = st.propagate_columns([small["psi"], small["phi"]], 30.0, 2, method, 6, comp.SUZUKI)
+    for got, psi in zip(many, (small["psi"], small["phi"])):
+        want = st.propagate(psi, 30.0, 2, method, 6, comp.SUZUKI)
+        assert np.linalg.norm(got - want) < 1e-12
