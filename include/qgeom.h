@@ -68,17 +68,43 @@ typedef enum {
   QG_ERR_UNSUPPORTED = 6
 } qg_status;
 
-/* Elementary second-order methods (Sec. II B). */
+/* Elementary second-order methods (Sec. II B), composable (Sec. II C). */
 enum { QG_TRAPEZOIDAL = 0,   /* U_impl(dt/2) U_expl(dt/2), Eq. (trap_rule)    */
-       QG_MIDPOINT = 1 };    /* U_expl(dt/2) U_impl(dt/2), Eq. (imp_midpoint) */
+       QG_MIDPOINT = 1,      /* U_expl(dt/2) U_impl(dt/2), Eq. (imp_midpoint) */
+/* The elementary comparison methods of Sec. II B, never composed.  Pass
+ * order 1 for the Euler methods and order 2 for SOD (the scheme is ignored);
+ * each step has size dt:
+ *   QG_EXPLICIT_EULER  psi' = (1 - i dt H) psi, Eq. (exp_euler): norm grows,
+ *                      unstable for every dt (Eq. exp_eu_stability);
+ *   QG_IMPLICIT_EULER  (1 + i dt H) psi' = psi, Eq. (imp_euler): one implicit
+ *                      solve with tau = dt per step, norm decays;
+ *   QG_SOD             psi(t + dt) = psi(t - dt) - 2 i dt H psi(t),
+ *                      Eq. (sod_method): stable only for dt < 1 / E_max
+ *                      (Eq. sod_critical_timestep).  Every call starts from
+ *                      psi(-dt) approximated by one two-stage Runge-Kutta
+ *                      step backward from the state (Sec. III), so nsteps in
+ *                      one call differ from the same steps split over calls.
+ * None of them is available for adjoint runs or qg_propagate_noalloc. */
+       QG_EXPLICIT_EULER = 2,
+       QG_IMPLICIT_EULER = 3,
+       QG_SOD = 4 };
 /* Composition schemes (Sec. II C). */
 enum { QG_TRIPLE_JUMP = 0,   /* Eq. (triple_jump), M = 3, C = 3^(order/2-1)     */
-       QG_SUZUKI = 1 };      /* Eq. (suzukis_fractal), M = 5, C = 5^(order/2-1) */
+       QG_SUZUKI = 1,        /* Eq. (suzukis_fractal), M = 5, C = 5^(order/2-1) */
+       /* the non-recursive "optimal" schemes of Sec. II C: Kahan and Li's
+        * minimal max|gamma_n| compositions, C = 9 for order 6 and C = 17 for
+        * order 8 (coefficients from Kahan & Li 1997, which the paper cites
+        * but does not print); order 4 is Suzuki's fractal, which Sec. II C
+        * names the optimal fourth-order scheme; order 2 the elementary step */
+       QG_OPTIMAL = 2 };
 /* State precision: the state is always stored in complex128.  QG_C128 solves
  * every implicit step in FP64.  QG_C64_MIXED runs the Krylov iterations in
  * complex64 and refines in FP64: r = b - (1 + i tau H) x is evaluated in FP64,
  * (1 + i tau H) d = r is solved in complex64 GMRES to inner_tol, x += d, until
- * ||r|| <= tol ||b|| (FP64 residual), so the result meets the same tolerance.
+ * ||r|| <= tol ||b|| (FP64 residual), so the result meets the same tolerance
+ * -- or until the FP64 residual stops falling (less than halved by a
+ * refinement step) within 256 DBL_EPSILON ||b|| (5.7e-14 ||b||), the rounding level of an
+ * FP64 residual; max_residual of the statistics reports what was reached.
  * Compositions, the state update and the observables stay FP64. */
 enum { QG_C128 = 0, QG_C64_MIXED = 1 };
 
@@ -331,8 +357,10 @@ void qg_batch_destroy(qg_batch_t b);
  * beyond the capacity return QG_ERR_INVALID_ARG with a message in
  * qg_last_error_string().  Every call shares the one array, whose contents
  * persist between calls (nothing in it needs to start at zero: each call
- * rewrites what it reads); calls that overlap on the GPU, on any stream or
- * thread, race and corrupt each other's results. */
+ * rewrites what it reads).  Calls that overlapped on the GPU would race on
+ * the array and corrupt each other's results; the library holds a per-device
+ * lock from the start of a call until its stream has finished, so calls
+ * from several host threads of one process run one after another. */
 qg_status qg_propagate_noalloc(int N, double qmin, double qmax, int S, double mass, const double* V,
                                const double* F, void* psi, int method, int order, int scheme, double dt,
                                int64_t nsteps, const qg_solver_opts* opts, qg_step_stats* stats,

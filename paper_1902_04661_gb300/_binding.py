@@ -25,8 +25,12 @@ QG_ERR_TIMEOUT = 5
 QG_ERR_UNSUPPORTED = 6
 QG_TRAPEZOIDAL = 0
 QG_MIDPOINT = 1
+QG_EXPLICIT_EULER = 2
+QG_IMPLICIT_EULER = 3
+QG_SOD = 4
 QG_TRIPLE_JUMP = 0
 QG_SUZUKI = 1
+QG_OPTIMAL = 2
 QG_C128 = 0
 QG_C64_MIXED = 1
 QG_SOLVER_GMRES = 0

@@ -149,29 +149,65 @@ bool valid_opts(const qg_solver_opts& o) {
          (o.guess == QG_GUESS_EULER || o.guess == QG_GUESS_ZERO);
 }
 
-// Composition fractions (Sec. II C): order 2 is the elementary step; each
-// recursion level maps the list L of order p to gamma_1 L, ..., gamma_M L
-// with the coefficients of Eq. (triple_jump) or Eq. (suzukis_fractal).
-bool make_schedule(int order, int scheme, std::vector<double>& fr) {
-  if (order < 2 || order > 8 || (order & 1)) return false;
-  if (scheme != QG_TRIPLE_JUMP && scheme != QG_SUZUKI) return false;
-  fr.assign(1, 1.0);
+// Composition fractions (Sec. II C) into a fixed array (no heap): order 2 is
+// the elementary step; for the recursive schemes each level maps the list L
+// of order p to gamma_1 L, ..., gamma_M L with the coefficients of
+// Eq. (triple_jump) or Eq. (suzukis_fractal).  QG_OPTIMAL is one
+// non-recursive palindrome of Kahan and Li's coefficients (M = 9 for order 6,
+// M = 17 for order 8), Suzuki's fractal for order 4.  Returns the count, or 0
+// for an invalid order / scheme.
+int schedule_fixed(int order, int scheme, double* out) {
+  if (order < 2 || order > 8 || (order & 1)) return 0;
+  if (scheme != QG_TRIPLE_JUMP && scheme != QG_SUZUKI && scheme != QG_OPTIMAL) return 0;
+  if (scheme == QG_OPTIMAL && order >= 6) {
+    // Kahan & Li (1997), first half of the palindrome, middle coefficient last
+    static const double kl6[5] = {0.39216144400731413927925056, 0.33259913678935943859974864,
+                                  -0.70624617255763935980996482, 0.08221359629355080023149045,
+                                  0.79854399093482996339895035};
+    static const double kl8[9] = {0.13020248308889008087881763,  0.56116298177510838456196441,
+                                  -0.38947496264484728640807860, 0.15884190655515560089621075,
+                                  -0.39590389413323757733623154, 0.18453964097831570709183254,
+                                  0.25837438768632204729397911,  0.29501172360931029887096624,
+                                  -0.60550853383003451169892108};
+    const double* h = order == 6 ? kl6 : kl8;
+    const int half = order == 6 ? 5 : 9, M = 2 * half - 1;
+    for (int i = 0; i < M; ++i) out[i] = h[i < half ? i : M - 1 - i];
+    return M;
+  }
+  if (scheme == QG_OPTIMAL) scheme = QG_SUZUKI;
+  double tmp[QG_MAX_FRACTIONS];
+  int cnt = 1;
+  out[0] = 1.0;
   for (int p = 2; p < order; p += 2) {
-    std::vector<double> g;
+    double g[5];
+    int M;
     if (scheme == QG_TRIPLE_JUMP) {
       const double r = std::pow(2.0, 1.0 / (p + 1));
-      g = {1.0 / (2.0 - r), -r / (2.0 - r), 1.0 / (2.0 - r)};
+      g[0] = g[2] = 1.0 / (2.0 - r);
+      g[1] = -r / (2.0 - r);
+      M = 3;
     } else {
       const double r = std::pow(4.0, 1.0 / (p + 1));
-      const double a = 1.0 / (4.0 - r);
-      g = {a, a, -r / (4.0 - r), a, a};
+      g[0] = g[1] = g[3] = g[4] = 1.0 / (4.0 - r);
+      g[2] = -r / (4.0 - r);
+      M = 5;
     }
-    std::vector<double> nx;
-    for (double gi : g)
-      for (double f : fr) nx.push_back(gi * f);
-    fr.swap(nx);
+    if (cnt * M > QG_MAX_FRACTIONS) return 0;
+    int k = 0;
+    for (int a = 0; a < M; ++a)
+      for (int b = 0; b < cnt; ++b) tmp[k++] = g[a] * out[b];
+    for (int b = 0; b < k; ++b) out[b] = tmp[b];
+    cnt = k;
   }
-  return (int)fr.size() <= QG_MAX_FRACTIONS;
+  return cnt;
+}
+
+bool make_schedule(int order, int scheme, std::vector<double>& fr) {
+  double buf[QG_MAX_FRACTIONS];
+  const int n = schedule_fixed(order, scheme, buf);
+  if (n <= 0) return false;
+  fr.assign(buf, buf + n);
+  return true;
 }
 
 InstDesc make_desc(const qg_state* s) {
@@ -646,10 +682,16 @@ static qg_status build_plan(int method, int order, int scheme, double dt, int64_
   default_opts(&o);
   if (opts) o = *opts;
   if (!valid_opts(o)) return QG_ERR_INVALID_ARG;
-  if (method != QG_TRAPEZOIDAL && method != QG_MIDPOINT) return QG_ERR_INVALID_ARG;
+  if (method < QG_TRAPEZOIDAL || method > QG_SOD) return QG_ERR_INVALID_ARG;
   if (!std::isfinite(dt) || nsteps < 0) return QG_ERR_INVALID_ARG;
   std::vector<double> fr;
-  if (!make_schedule(order, scheme, fr)) return QG_ERR_INVALID_ARG;
+  if (method >= QG_EXPLICIT_EULER) {
+    // the elementary comparison methods: one step of size dt, never composed
+    if (order != (method == QG_SOD ? 2 : 1)) return QG_ERR_INVALID_ARG;
+    fr.assign(1, 1.0);
+  } else if (!make_schedule(order, scheme, fr)) {
+    return QG_ERR_INVALID_ARG;
+  }
   memset(P, 0, sizeof(*P));
   P->method = method;
   P->nfrac = (int)fr.size();
@@ -673,7 +715,8 @@ static qg_status check_run(int run, const StepPlan& P, const qg_state* s) {
   if (run != QG_RUN_FORWARD && run != QG_RUN_CHECKPOINT && run != QG_RUN_ADJOINT) return QG_ERR_INVALID_ARG;
   if (run == QG_RUN_CHECKPOINT && (!s->adj.ckpt || s->adj.every < 1 || s->adj.nckpt < 1)) return QG_ERR_INVALID_ARG;
   if (run == QG_RUN_ADJOINT &&
-      (!s->adj.grad || !s->adj.gV || !s->adj.gF || P.restart > QG_MAX_RESTART - 4 || s->adj.every < 1))
+      (!s->adj.grad || !s->adj.gV || !s->adj.gF || P.restart > QG_MAX_RESTART - 4 || s->adj.every < 1 ||
+       P.method >= QG_EXPLICIT_EULER))
     return QG_ERR_INVALID_ARG;
   return QG_OK;
 }
@@ -1026,37 +1069,6 @@ qg_status qg_overlap(qg_state_t a, qg_state_t b, double* out) {
   return QG_OK;
 }
 
-// Composition fractions into a fixed array (no heap): same recursion as
-// make_schedule.  Returns the count, or 0 for an invalid order / scheme.
-static int schedule_fixed(int order, int scheme, double* out) {
-  if (order < 2 || order > 8 || (order & 1)) return 0;
-  if (scheme != QG_TRIPLE_JUMP && scheme != QG_SUZUKI) return 0;
-  double tmp[QG_MAX_FRACTIONS];
-  int cnt = 1;
-  out[0] = 1.0;
-  for (int p = 2; p < order; p += 2) {
-    double g[5];
-    int M;
-    if (scheme == QG_TRIPLE_JUMP) {
-      const double r = std::pow(2.0, 1.0 / (p + 1));
-      g[0] = g[2] = 1.0 / (2.0 - r);
-      g[1] = -r / (2.0 - r);
-      M = 3;
-    } else {
-      const double r = std::pow(4.0, 1.0 / (p + 1));
-      g[0] = g[1] = g[3] = g[4] = 1.0 / (4.0 - r);
-      g[2] = -r / (4.0 - r);
-      M = 5;
-    }
-    if (cnt * M > QG_MAX_FRACTIONS) return 0;
-    int k = 0;
-    for (int a = 0; a < M; ++a)
-      for (int b = 0; b < cnt; ++b) tmp[k++] = g[a] * out[b];
-    for (int b = 0; b < k; ++b) out[b] = tmp[b];
-    cnt = k;
-  }
-  return cnt;
-}
 
 qg_status qg_propagate_noalloc(int N, double qmin, double qmax, int S, double mass, const double* V, const double* F,
                                void* psi, int method, int order, int scheme, double dt, int64_t nsteps,

@@ -1,6 +1,8 @@
 // The no-allocation entry point's kernels and launch wrapper.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "qg_dom1d.cuh"
 
 // ---------------------------------------------------------------------------
@@ -14,7 +16,9 @@
 // memory from cudaMalloc.  Capacity: S * N <= QG_NA_MAX_LEN complex values,
 // N <= QG_NA_MAX_N, GMRES restart length <= QG_NA_MAX_RESTART.  The array
 // (about 3 MB) stays resident on every GPU that loads the library until the
-// process exits.  All calls share it: calls that overlap on the GPU race.
+// process exits.  All calls share it: calls that overlap on the GPU would
+// race on it, so the host side holds a per-device lock from the start of a
+// call until its stream has finished.
 
 namespace qg {
 
@@ -114,9 +118,13 @@ __global__ void __launch_bounds__(QG_THREADS, 1)
 
 }  // namespace qg
 
-// Per-device set-up state of the no-allocation entry point (host side).
+// Per-device set-up state of the no-allocation entry point (host side),
+// guarded by the device's lock.  The tables' key (n, dq) is recorded only
+// after the call's stream has finished, so a key always names tables that
+// are complete in device memory.
 namespace {
 constexpr int kNaMaxDevices = 64;
+std::mutex g_na_lock[kNaMaxDevices];
 unsigned char* g_na_ptr[kNaMaxDevices] = {nullptr};
 int g_na_tab_n[kNaMaxDevices] = {0};
 double g_na_tab_dq[kNaMaxDevices] = {0.0};
@@ -129,6 +137,8 @@ cudaError_t qg_noalloc_launch(int n, double qmin, double qmax, int S, double mas
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+  // one call at a time per device: the scratch array is shared by every call
+  std::lock_guard<std::mutex> hold(g_na_lock[dev]);
   if (!g_na_ptr[dev]) {
     // The symbol's name in host code is only a stand-in: take the device
     // address of this device's copy once, with the device current.
@@ -140,12 +150,12 @@ cudaError_t qg_noalloc_launch(int n, double qmin, double qmax, int S, double mas
   }
   unsigned char* base = g_na_ptr[dev];
   const double dq = (qmax - qmin) / n;
-  if (g_na_tab_n[dev] != n || g_na_tab_dq[dev] != dq) {
+  const bool rebuild = g_na_tab_n[dev] != n || g_na_tab_dq[dev] != dq;
+  if (rebuild) {
+    g_na_tab_n[dev] = 0;   // invalid until this call's stream has finished
     qg::noalloc_tables_kernel<<<(n + 255) / 256, 256, 0, st>>>(base, plan, dq);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    g_na_tab_n[dev] = n;
-    g_na_tab_dq[dev] = dq;
   }
   size_t smem;
   const int nb = nb_capacity(n, S, P.restart, &smem);
@@ -167,6 +177,11 @@ cudaError_t qg_noalloc_launch(int n, double qmin, double qmax, int S, double mas
   e = cudaMemcpyAsync(host_stats, base + qg::kNaWorkBytes + qg::kNaTwBytes + qg::kNaKdBytes, sizeof(qg_step_stats),
                       cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(st);
+  e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && rebuild) {
+    g_na_tab_n[dev] = n;
+    g_na_tab_dq[dev] = dq;
+  }
+  return e;
 }
 

@@ -77,3 +77,18 @@ def test_mixed_not_converged_restores(qglib, cuda):
     s = st.propagate(qglib.QG_TRAPEZOIDAL, 2, 0, 3000.0 * FS, 2, opts, allow_fail=True)
     assert s["status"] == qglib.QG_ERR_NOT_CONVERGED
     np.testing.assert_array_equal(st.get(), before)
+
+
+def test_mixed_order2_midpoint_hpsi_counts(qglib, cuda):
+    # with a single fraction per step the mixed form starts each solve from a
+    # complex64 explicit-Euler step and forms every FP64 residual exactly: one
+    # FP64 H psi per refinement step plus the final check, one complex64 H psi
+    # for the start plus one per inner iteration or inner restart
+    n = 512
+    grid, model = nai_library_model(qglib, n)
+    st = qglib.State(model, precision=qglib.QG_C64_MIXED)
+    st.set_gaussian(1, [wl.NAI_Q0], [1.0], [wl.NAI_SIGMA0])
+    s = st.propagate(qglib.QG_MIDPOINT, 2, qglib.QG_SUZUKI, 0.5 * FS, 20, qglib.default_solver_opts(tol=1e-13))
+    assert s["n_substeps"] == 20
+    assert s["n_hpsi"] == s["n_outer"] + s["n_substeps"]
+    assert s["n_hpsi32"] == s["n_substeps"] + s["n_krylov"] + s["n_restart"]

@@ -24,7 +24,7 @@ def _small_setup(qglib):
 
 
 @pytest.mark.parametrize("method", [0, 1])
-@pytest.mark.parametrize("order,scheme", [(2, 0), (4, 0), (4, 1), (6, 0), (6, 1), (8, 0), (8, 1)])
+@pytest.mark.parametrize("order,scheme", [(2, 0), (4, 0), (4, 1), (6, 0), (6, 1), (8, 0), (8, 1), (6, 2), (8, 2)])
 def test_composed_steps_vs_oracle(qglib, cuda, method, order, scheme):
     grid, model, H, psi0 = _small_setup(qglib)
     dt = 1.0 * FS

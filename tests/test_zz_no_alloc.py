@@ -46,6 +46,54 @@ def test_noalloc_matches_qg_propagate_on_two_calls(qglib, cuda):
         assert rel_l2(psi.cpu().numpy(), reg.get()) < 1e-11
 
 
+def _model_case(qg, torch, n, qmin, qmax, S, mass, W, dW):
+    grid = qg.Grid([n], [qmin], [qmax])
+    model = qg.Model(grid, S, [mass], W=W, dW=dW)
+    Vh, Fh = model.fields()
+    return grid, model, torch.tensor(Vh, device="cuda"), torch.tensor(Fh, device="cuda")
+
+
+def test_noalloc_rebuilds_tables_between_grids_and_runs_s3_trapezoidal(qglib, cuda):
+    # a call on another grid rebuilds the FFT tables kept in the shared array;
+    # going back to the first grid rebuilds them again; an S = 3 model with
+    # the trapezoidal rule uses the workspace with B as right-hand side
+    torch = cuda
+    mass = wl.NAI_REDUCED_MASS
+    opts = qglib.default_solver_opts(tol=1e-14, restart=16)
+    dt = 0.5 * FS
+    cases = [(2048, wl.NAI_QMIN, wl.NAI_QMAX), (1024, wl.NAI_QMIN, 30.0), (2048, wl.NAI_QMIN, wl.NAI_QMAX)]
+    for n, qmin, qmax in cases:
+        q = qmin + (qmax - qmin) / n * np.arange(n)
+        W, dW = wl.nai_like_diabatic(q)
+        keep = _model_case(qglib, torch, n, qmin, qmax, 2, mass, W, dW)
+        grid, model, V, F = keep
+        reg = qglib.State(model)
+        reg.set_gaussian(1, [wl.NAI_Q0], [2.0], [wl.NAI_SIGMA0])
+        psi = torch.tensor(reg.get(), device="cuda")
+        reg.propagate(qglib.QG_MIDPOINT, 4, qglib.QG_SUZUKI, dt, 2, opts)
+        r, s_na = _call(qglib, torch, n, qmin, qmax, 2, mass, V, F, psi, qglib.QG_MIDPOINT, 4, qglib.QG_SUZUKI,
+                        dt, 2, opts)
+        assert r == qglib.QG_OK, qglib.lib().qg_last_error_string()
+        assert s_na.status == 0
+        assert rel_l2(psi.cpu().numpy(), reg.get()) < 1e-11
+    seed = 1000
+    while True:
+        m = wl.avoided_crossing_model(seed)
+        if m["S"] == 3 and m["N"] <= 2048:
+            break
+        seed += 1
+    grid, model, V, F = _model_case(qglib, torch, m["N"], m["qmin"], m["qmax"], 3, m["mass"], m["W"], m["dW"])
+    reg = qglib.State(model)
+    reg.set_gaussian(m["surface"], [m["q0"]], [m["p0"]], [m["sigma0"]])
+    psi = torch.tensor(reg.get(), device="cuda")
+    reg.propagate(qglib.QG_TRAPEZOIDAL, 4, qglib.QG_TRIPLE_JUMP, 0.1 * FS, 3, opts)
+    r, s_na = _call(qglib, torch, m["N"], m["qmin"], m["qmax"], 3, m["mass"], V, F, psi, qglib.QG_TRAPEZOIDAL, 4,
+                    qglib.QG_TRIPLE_JUMP, 0.1 * FS, 3, opts)
+    assert r == qglib.QG_OK, qglib.lib().qg_last_error_string()
+    assert s_na.status == 0 and s_na.n_substeps == 9
+    assert rel_l2(psi.cpu().numpy(), reg.get()) < 1e-11
+
+
 def test_noalloc_rejects_sizes_beyond_its_capacity(qglib, cuda):
     torch = cuda
     n = 8192
