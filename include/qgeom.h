@@ -223,6 +223,21 @@ qg_status qg_state_set_stream(qg_state_t s, void* stream);
  * trial), keeps the fastest and writes the three trial times (ms) to ms_out
  * (may be NULL).  No effect on 1-D states, which run on one CTA each. */
 qg_status qg_state_set_launch_width(qg_state_t s, int ctas);
+/* 1-D grids: the launch form of the state's propagations (not in the paper;
+ * the same arithmetic as the default form).  G = 0 (default): one CTA owns
+ * the instance and keeps its vectors in global memory.  G = 1, 2, 4, 8, 16:
+ * the shared-memory cluster form -- a thread-block cluster of G CTAs owns the
+ * instance, CTA r holds the grid points j = r + G n2 of every surface, every
+ * solver vector lives in shared memory, the spectral derivative (Sec. II D)
+ * takes a length-N/G transform in each CTA plus length-G transforms across
+ * the cluster through distributed shared memory, and sums over the state are
+ * combined across the cluster in a fixed order.  Needs a QG_C128 state,
+ * S * N / G <= 1024, N / G >= 8; applies to forward runs (checkpoint and
+ * adjoint runs keep the one-CTA form).  QG_ERR_UNSUPPORTED otherwise.
+ * qg_cluster_size gives the smallest G that holds an instance of N points and
+ * S surfaces (0: none). */
+qg_status qg_state_set_cluster(qg_state_t s, int G);
+int qg_cluster_size(int N, int S, int restart);
 qg_status qg_state_autotune(qg_state_t s, int method, int order, int scheme, double dt, int64_t trial_steps,
                             const qg_solver_opts* opts, double* ms_out);
 qg_status qg_set_state(qg_state_t s, const void* psi, int on_device);
@@ -322,14 +337,20 @@ qg_status qg_batch_replay(qg_batch_t b);
 /* Autotuner of the batched launch (not in the paper): times trial_steps
  * composed steps of the real batch under each candidate launch shape --
  * {1, 2} CTAs per SM x {all surfaces of an instance per shared-memory FFT
- * batch, one surface at a time} -- restoring every state after each trial,
- * and keeps the fastest for later qg_batch_run / qg_batch_capture calls (a
- * captured graph is dropped).  ms_out (4 doubles, may be NULL) receives the
- * trial times in that order, -1 for a shape that does not fit.
- * qg_batch_tuning reports the chosen shape (surfaces_per_fft 0 = all). */
+ * batch, one surface at a time} for the one-CTA form, then the shared-memory
+ * cluster form (see qg_state_set_cluster) at the smallest cluster size that
+ * holds every instance and at twice that size -- restoring every state after
+ * each trial, and keeps the fastest for later qg_batch_run /
+ * qg_batch_capture calls (a captured graph is dropped).  ms_out (6 doubles,
+ * may be NULL) receives the trial times in that order, -1 for a shape that
+ * does not fit.  qg_batch_tuning reports the chosen one-CTA shape
+ * (surfaces_per_fft 0 = all), qg_batch_cluster the chosen cluster size (0 =
+ * the one-CTA form); qg_batch_set_cluster sets it by hand. */
 qg_status qg_batch_autotune(qg_batch_t b, int method, int order, int scheme, double dt, int64_t trial_steps,
                             const qg_solver_opts* opts, double* ms_out);
 qg_status qg_batch_tuning(qg_batch_t b, int* ctas_per_sm, int* surfaces_per_fft);
+qg_status qg_batch_cluster(qg_batch_t b, int* G);
+qg_status qg_batch_set_cluster(qg_batch_t b, int G);
 qg_status qg_batch_stats(qg_batch_t b, int32_t* statuses, qg_step_stats* stats);
 void* qg_batch_stream(qg_batch_t b);
 void qg_batch_destroy(qg_batch_t b);

@@ -129,6 +129,10 @@ def lib():
             "qg_batch_tuning": (I, [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
             "qg_selftest_barrier_timeout": (I, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
             "qg_state_set_launch_width": (I, [P, I]),
+            "qg_state_set_cluster": (I, [P, I]),
+            "qg_cluster_size": (I, [I, I, I]),
+            "qg_batch_cluster": (I, [P, ctypes.POINTER(ctypes.c_int)]),
+            "qg_batch_set_cluster": (I, [P, I]),
             "qg_state_autotune": (I, [P, I, I, I, D, ctypes.c_int64, ctypes.POINTER(SolverOpts),
                                       ctypes.POINTER(ctypes.c_double)]),
             "qg_batch_destroy": (V, [P]),
@@ -325,6 +329,11 @@ class State:
         """2-D states: CTAs of the cooperative launch (0 = automatic)."""
         _check(lib().qg_state_set_launch_width(self.handle, int(ctas)), "qg_state_set_launch_width")
 
+    def set_cluster(self, G):
+        """1-D states: G = 0 one CTA with vectors in global memory; G = 1, 2,
+        4, 8, 16 the shared-memory cluster form with G CTAs per instance."""
+        _check(lib().qg_state_set_cluster(self.handle, int(G)), "qg_state_set_cluster")
+
     def autotune(self, method, order, scheme, dt, trial_steps=1, opts=None):
         """2-D states: pick the fastest cooperative launch width; returns the
         trial times (ms) at the automatic width, 1/2 and 1/4 of it."""
@@ -409,14 +418,26 @@ class Batch:
 
     def autotune(self, method, order, scheme, dt, trial_steps=1, opts=None):
         """Pick the fastest launch shape on the real batch; returns the trial
-        times (ms) of {1, 2} CTAs/SM x {all surfaces, one surface} per FFT."""
+        times (ms) of {1, 2} CTAs/SM x {all surfaces, one surface} per FFT,
+        then of the shared-memory cluster form at the smallest cluster size
+        and at twice it (-1: does not fit)."""
         o = opts if opts is not None else default_solver_opts()
-        ms = (ctypes.c_double * 4)()
+        ms = (ctypes.c_double * 6)()
         _check(lib().qg_batch_autotune(self.handle, method, order, scheme, float(dt), int(trial_steps),
                                        ctypes.byref(o), ms), "qg_batch_autotune")
         c, s = ctypes.c_int(), ctypes.c_int()
         _check(lib().qg_batch_tuning(self.handle, ctypes.byref(c), ctypes.byref(s)), "qg_batch_tuning")
-        return {"trial_ms": list(ms), "ctas_per_sm": c.value, "surfaces_per_fft": s.value}
+        return {"trial_ms": list(ms), "ctas_per_sm": c.value, "surfaces_per_fft": s.value, "cluster": self.cluster}
+
+    @property
+    def cluster(self):
+        """Cluster size of the shared-memory cluster form (0: one-CTA form)."""
+        g = ctypes.c_int()
+        _check(lib().qg_batch_cluster(self.handle, ctypes.byref(g)), "qg_batch_cluster")
+        return g.value
+
+    def set_cluster(self, G):
+        _check(lib().qg_batch_set_cluster(self.handle, int(G)), "qg_batch_set_cluster")
 
     @property
     def stream(self):
@@ -426,6 +447,12 @@ class Batch:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.qg_batch_destroy(self.handle)
             self.handle = None
+
+
+def cluster_size(N, S, restart=30):
+    """Smallest cluster size of the shared-memory cluster form that holds an
+    instance of N points and S surfaces (0: none)."""
+    return int(lib().qg_cluster_size(int(N), int(S), int(restart)))
 
 
 def qg_version():

@@ -12,8 +12,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libqgeom.so")
 # (source, object, extra flags): the persistent 1-D propagator is compiled once
-# per occupancy and the 2-D one once per precision form, so the large
-# instantiations build in parallel.  In the 2-D kernels CTAs read data other
+# per occupancy, its shared-memory cluster form once per cluster size and the
+# 2-D one once per precision form, so the large instantiations build in
+# parallel.  In the 2-D kernels CTAs read data other
 # CTAs wrote in the same launch, so their global loads are cached in L2 only.
 UNITS = [
     ("qg_propagate.cu", "qg_propagate_b1.o", ["-DQG_MINB=1"]),
@@ -21,6 +22,11 @@ UNITS = [
     ("qg_propagate2d.cu", "qg_propagate2d_f64.o", ["-DQG_PREC=0", "-Xptxas", "-dlcm=cg"]),
     ("qg_propagate2d.cu", "qg_propagate2d_mixed.o", ["-DQG_PREC=1", "-Xptxas", "-dlcm=cg"]),
     ("qg_kernels2d.cu", "qg_kernels2d.o", ["-Xptxas", "-dlcm=cg"]),
+    ("qg_propagate_cluster.cu", "qg_propagate_cluster_g1.o", ["-DQG_CLUSTER_G=1"]),
+    ("qg_propagate_cluster.cu", "qg_propagate_cluster_g2.o", ["-DQG_CLUSTER_G=2"]),
+    ("qg_propagate_cluster.cu", "qg_propagate_cluster_g4.o", ["-DQG_CLUSTER_G=4"]),
+    ("qg_propagate_cluster.cu", "qg_propagate_cluster_g8.o", ["-DQG_CLUSTER_G=8"]),
+    ("qg_propagate_cluster.cu", "qg_propagate_cluster_g16.o", ["-DQG_CLUSTER_G=16"]),
     ("qg_noalloc.cu", "qg_noalloc.o", []),
     ("qg_kernels.cu", "qg_kernels.o", []),
     ("qg_api.cu", "qg_api.o", []),

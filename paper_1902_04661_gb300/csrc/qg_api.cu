@@ -566,6 +566,17 @@ void qg_destroy_state(qg_state_t s) {
   delete s;
 }
 
+qg_status qg_state_set_cluster(qg_state_t s, int G) {
+  if (!s || G < 0) return QG_ERR_INVALID_ARG;
+  if (G > 0) {
+    const qg_grid* g = s->m->g;
+    if (g->D != 1 || s->precision != QG_C128) return QG_ERR_UNSUPPORTED;
+    if (qg_cluster_smem(g->n[0], s->m->S, G, 4) == 0) return QG_ERR_UNSUPPORTED;
+  }
+  s->cluster = G;
+  return QG_OK;
+}
+
 qg_status qg_state_set_launch_width(qg_state_t s, int ctas) {
   if (!s || ctas < 0) return QG_ERR_INVALID_ARG;
   s->launch_ctas = ctas;
@@ -746,6 +757,10 @@ qg_status qg_propagate_ex(qg_state_t s, int run, int method, int order, int sche
   if (g->D == 2) {
     if (run == QG_RUN_ADJOINT || P.restart > QG_MAX_RESTART - 1) return QG_ERR_UNSUPPORTED;
     QG_TRY(qg_launch_propagate2d(make_inst2d(s), P, s->d_stats, s->stream));
+  } else if (s->cluster > 0 && run == QG_RUN_FORWARD) {
+    const size_t smem = qg_cluster_smem(g->n[0], s->m->S, s->cluster, P.restart);
+    if (smem == 0) return QG_ERR_UNSUPPORTED;
+    QG_TRY(qg_launch_cluster(s->cluster, s->d_inst, 1, P, s->d_stats, smem, s->stream));
   } else {
     QG_TRY(qg_launch_propagate(s->d_inst, 1, P, s->d_counter, s->d_stats, g->n[0], s->m->S, s->stream));
   }
@@ -766,6 +781,10 @@ qg_status qg_propagate(qg_state_t s, int method, int order, int scheme, double d
   if (g->D == 2) {
     if (P.restart > QG_MAX_RESTART - 1) return QG_ERR_UNSUPPORTED;
     QG_TRY(qg_launch_propagate2d(make_inst2d(s), P, s->d_stats, s->stream));
+  } else if (s->cluster > 0) {
+    const size_t smem = qg_cluster_smem(g->n[0], s->m->S, s->cluster, P.restart);
+    if (smem == 0) return QG_ERR_UNSUPPORTED;
+    QG_TRY(qg_launch_cluster(s->cluster, s->d_inst, 1, P, s->d_stats, smem, s->stream));
   } else {
     QG_TRY(qg_launch_propagate(s->d_inst, 1, P, s->d_counter, s->d_stats, g->n[0], s->m->S, s->stream));
   }
@@ -802,10 +821,16 @@ qg_status qg_batch_create(qg_state_t* states, int nstates, qg_batch_t* out) {
   }
   std::vector<InstDesc> descs(nstates);
   std::vector<double> cost(nstates);
+  b->all_fp64 = 1;
+  b->min_n = 1 << 30;
   for (int i = 0; i < nstates; ++i) {
     const InstDesc d = make_desc(states[i]);
     if (d.n > b->max_n) b->max_n = d.n;
     if (d.S > b->max_S) b->max_S = d.S;
+    if (d.n < b->min_n) b->min_n = d.n;
+    if (d.S * d.n > b->max_len) b->max_len = d.S * d.n;
+    if (d.precision != QG_C128) b->all_fp64 = 0;
+    b->nmask[d.S] |= 1u << ilog2h(d.n);
     // work estimate of one H psi: S transforms of n log2 n
     cost[i] = (double)d.S * d.n * (ilog2h(d.n) + 1);
     b->order[i] = i;
@@ -862,14 +887,40 @@ static qg_status batch_collect(qg_batch_t b, int32_t* statuses, qg_step_stats* s
   return ret;
 }
 
+// Largest dynamic shared memory any instance of the batch needs in the
+// cluster form of size G (0 if one does not fit).
+static size_t batch_cluster_smem(const qg_batch* b, int G, int restart) {
+  if (!b->all_fp64) return 0;
+  size_t best = 0;
+  for (int S = 2; S <= QG_MAX_S; ++S)
+    for (int k = 0; k < 31; ++k)
+      if (b->nmask[S] & (1u << k)) {
+        const size_t t = qg_cluster_smem(1 << k, S, G, restart);
+        if (t == 0) return 0;
+        best = std::max(best, t);
+      }
+  return best;
+}
+
+// One persistent launch of the batch in its current launch shape: the
+// cluster form for forward runs when chosen, else the one-CTA form.
+static cudaError_t batch_launch(qg_batch* b, const StepPlan& P, int ninst, int cluster, int ctas_per_sm, int nb_pref) {
+  if (cluster > 0 && P.run == QG_RUN_FORWARD) {
+    const size_t smem = batch_cluster_smem(b, cluster, P.restart);
+    if (smem == 0) return cudaErrorInvalidConfiguration;
+    return qg_launch_cluster(cluster, b->d_desc, ninst, P, b->d_stats, smem, b->stream);
+  }
+  return qg_launch_propagate_tuned(b->d_desc, ninst, P, b->d_counter, b->d_stats, b->max_n, b->max_S, ctas_per_sm,
+                                   nb_pref, b->stream);
+}
+
 qg_status qg_batch_run(qg_batch_t b, int method, int order, int scheme, double dt, int64_t nsteps,
                        const qg_solver_opts* opts, int32_t* statuses, qg_step_stats* stats) {
   if (!b) return QG_ERR_INVALID_ARG;
   StepPlan P;
   qg_status st = build_plan(method, order, scheme, dt, nsteps, opts, &P);
   if (st != QG_OK) return st;
-  QG_TRY(qg_launch_propagate_tuned(b->d_desc, b->n, P, b->d_counter, b->d_stats, b->max_n, b->max_S, b->ctas_per_sm,
-                                   b->nb_pref, b->stream));
+  QG_TRY(batch_launch(b, P, b->n, b->cluster, b->ctas_per_sm, b->nb_pref));
   return batch_collect(b, statuses, stats);
 }
 
@@ -883,8 +934,7 @@ qg_status qg_batch_run_ex(qg_batch_t b, int run, int method, int order, int sche
   if (run == QG_RUN_ADJOINT && P.restart > QG_MAX_RESTART - 4) return QG_ERR_INVALID_ARG;
   if (run != QG_RUN_FORWARD && !b->adjoint_ready) return QG_ERR_INVALID_ARG;
   P.run = run;
-  QG_TRY(qg_launch_propagate_tuned(b->d_desc, b->n, P, b->d_counter, b->d_stats, b->max_n, b->max_S, b->ctas_per_sm,
-                                   b->nb_pref, b->stream));
+  QG_TRY(batch_launch(b, P, b->n, b->cluster, b->ctas_per_sm, b->nb_pref));
   return batch_collect(b, statuses, stats);
 }
 
@@ -900,13 +950,11 @@ qg_status qg_batch_capture(qg_batch_t b, int method, int order, int scheme, doub
   }
   // function attributes are set here, outside the capture, by a zero-instance
   // launch that the kernel leaves immediately
-  QG_TRY(qg_launch_propagate_tuned(b->d_desc, 0, P, b->d_counter, b->d_stats, b->max_n, b->max_S, b->ctas_per_sm,
-                                   b->nb_pref, b->stream));
+  QG_TRY(batch_launch(b, P, 0, b->cluster, b->ctas_per_sm, b->nb_pref));
   QG_TRY(cudaStreamSynchronize(b->stream));
   cudaGraph_t g = nullptr;
   QG_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = qg_launch_propagate_tuned(b->d_desc, b->n, P, b->d_counter, b->d_stats, b->max_n, b->max_S,
-                                            b->ctas_per_sm, b->nb_pref, b->stream);
+  cudaError_t e = batch_launch(b, P, b->n, b->cluster, b->ctas_per_sm, b->nb_pref);
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
@@ -946,18 +994,27 @@ qg_status qg_batch_autotune(qg_batch_t b, int method, int order, int scheme, dou
     }
     return cudaSuccess;
   };
-  const int cand[4][2] = {{1, 0}, {1, 1}, {2, 0}, {2, 1}};
+  // {CTAs per SM, surfaces per FFT batch, cluster size}: the one-CTA form in
+  // four shapes, then the shared-memory cluster form at the smallest cluster
+  // that holds the largest instance and at twice that size
+  int g0 = 0;
+  for (int G = 1; G <= 16 && !g0; G *= 2)
+    if (batch_cluster_smem(b, G, P.restart) > 0) g0 = G;
+  const int cand[6][3] = {{1, 0, 0}, {1, 1, 0}, {2, 0, 0}, {2, 1, 0}, {1, 0, g0}, {1, 0, g0 > 0 && g0 < 16 ? 2 * g0 : 0}};
   double best = 1e300;
   int bi = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = copy_all(true);
-  for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+  for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
     float ms = -1.f;
+    if (c >= 4 && (cand[c][2] == 0 || batch_cluster_smem(b, cand[c][2], P.restart) == 0)) {
+      if (ms_out) ms_out[c] = -1.0;
+      continue;
+    }
     e = cudaEventRecord(e0, b->stream);
-    cudaError_t el = qg_launch_propagate_tuned(b->d_desc, b->n, P, b->d_counter, b->d_stats, b->max_n, b->max_S,
-                                               cand[c][0], cand[c][1], b->stream);
+    cudaError_t el = batch_launch(b, P, b->n, cand[c][2], cand[c][0], cand[c][1]);
     if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     if (el == cudaSuccess && e == cudaSuccess) {
@@ -985,6 +1042,7 @@ qg_status qg_batch_autotune(qg_batch_t b, int method, int order, int scheme, dou
   }
   b->ctas_per_sm = cand[bi][0];
   b->nb_pref = cand[bi][1];
+  b->cluster = cand[bi][2];
   if (b->graph) {   // a captured graph used the old launch shape
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -997,6 +1055,30 @@ qg_status qg_batch_tuning(qg_batch_t b, int* ctas_per_sm, int* surfaces_per_fft)
   if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
   if (surfaces_per_fft) *surfaces_per_fft = b->nb_pref;
   return QG_OK;
+}
+
+qg_status qg_batch_set_cluster(qg_batch_t b, int G) {
+  if (!b || G < 0) return QG_ERR_INVALID_ARG;
+  if (G > 0 && batch_cluster_smem(b, G, QG_MAX_RESTART) == 0 && batch_cluster_smem(b, G, 4) == 0)
+    return QG_ERR_UNSUPPORTED;
+  b->cluster = G;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return QG_OK;
+}
+
+qg_status qg_batch_cluster(qg_batch_t b, int* G) {
+  if (!b || !G) return QG_ERR_INVALID_ARG;
+  *G = b->cluster;
+  return QG_OK;
+}
+
+int qg_cluster_size(int N, int S, int restart) {
+  for (int G = 1; G <= 16; G *= 2)
+    if (qg_cluster_smem(N, S, G, restart) > 0) return G;
+  return 0;
 }
 
 qg_status qg_batch_replay(qg_batch_t b) {

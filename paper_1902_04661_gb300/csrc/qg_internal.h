@@ -78,6 +78,7 @@ struct qg_state {
   qg_state_adjoint adj;     // caller-owned adjoint buffers (or nulls)
   unsigned char* d_coop;    // 2-D grids: barrier words, error flag, partial sums
   int launch_ctas;          // 2-D grids: cooperative launch width (0 = automatic)
+  int cluster;              // 1-D grids: > 0 selects the shared-memory cluster form with this many CTAs
 };
 
 // Everything one CTA needs to work on one instance (a state with its model
@@ -174,6 +175,10 @@ struct qg_batch {
   bool adjoint_ready;       // every state has checkpoint and gradient buffers
   int ctas_per_sm;          // launch shape chosen by qg_batch_autotune (default 1)
   int nb_pref;              // surfaces per FFT batch (0 = as many as fit)
+  int cluster;              // > 0: the shared-memory cluster form with this many CTAs per instance
+  int all_fp64;             // every state is QG_C128 (the cluster form needs it)
+  int min_n, max_len;       // smallest grid and largest S * N of the batch
+  unsigned nmask[QG_MAX_S + 1];  // bit k of nmask[S]: an instance has S surfaces and 2^k points
 };
 
 // Launch wrappers (qg_kernels.cu).
@@ -195,6 +200,27 @@ cudaError_t qg_launch_propagate_minb<2>(const InstDesc*, int, const StepPlan&, i
 cudaError_t qg_launch_propagate_tuned(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
                                       qg_step_stats* d_stats, int max_n, int max_S, int ctas_per_sm, int nb_pref,
                                       cudaStream_t st);
+// The shared-memory cluster form of the 1-D propagator, one translation unit
+// per cluster size G (qg_propagate_cluster.cu); qg_launch_cluster dispatches
+// on G (1, 2, 4, 8, 16).
+template <int G>
+cudaError_t qg_launch_cluster_g(const InstDesc* d_insts, int ninst, const StepPlan& plan, qg_step_stats* d_stats,
+                                size_t smem, cudaStream_t st);
+template <>
+cudaError_t qg_launch_cluster_g<1>(const InstDesc*, int, const StepPlan&, qg_step_stats*, size_t, cudaStream_t);
+template <>
+cudaError_t qg_launch_cluster_g<2>(const InstDesc*, int, const StepPlan&, qg_step_stats*, size_t, cudaStream_t);
+template <>
+cudaError_t qg_launch_cluster_g<4>(const InstDesc*, int, const StepPlan&, qg_step_stats*, size_t, cudaStream_t);
+template <>
+cudaError_t qg_launch_cluster_g<8>(const InstDesc*, int, const StepPlan&, qg_step_stats*, size_t, cudaStream_t);
+template <>
+cudaError_t qg_launch_cluster_g<16>(const InstDesc*, int, const StepPlan&, qg_step_stats*, size_t, cudaStream_t);
+cudaError_t qg_launch_cluster(int G, const InstDesc* d_insts, int ninst, const StepPlan& plan, qg_step_stats* d_stats,
+                              size_t smem, cudaStream_t st);
+// Dynamic shared memory of the cluster form for an instance of n points and
+// S surfaces on clusters of G CTAs, or 0 if that shape is not supported.
+size_t qg_cluster_smem(int n, int S, int G, int restart);
 cudaError_t qg_launch_apply_h(const InstDesc* d_inst, double2* d_out, int n, int S, cudaStream_t st);
 cudaError_t qg_launch_energy(const InstDesc* d_inst, double* d_out, int n, int S, cudaStream_t st);
 cudaError_t qg_launch_populations(const double2* d_psi, int n, int S, double dq, double* d_out, cudaStream_t st);

@@ -4,6 +4,7 @@
 // occupancy dispatch of the persistent propagator.
 #include <cuda_runtime.h>
 
+#include "qg_cluster.cuh"
 #include "qg_dom1d.cuh"
 
 namespace qg {
@@ -327,4 +328,31 @@ cudaError_t qg_launch_fields2(const double* d_W, const double* d_dW, int n, int 
                               cudaStream_t st) {
   qg::fields2_kernel<<<(n + 255) / 256, 256, 0, st>>>(d_W, d_dW, n, D, d_V, d_F);
   return cudaGetLastError();
+}
+
+cudaError_t qg_launch_cluster(int G, const InstDesc* d_insts, int ninst, const StepPlan& plan, qg_step_stats* d_stats,
+                              size_t smem, cudaStream_t st) {
+  switch (G) {
+    case 1:
+      return qg_launch_cluster_g<1>(d_insts, ninst, plan, d_stats, smem, st);
+    case 2:
+      return qg_launch_cluster_g<2>(d_insts, ninst, plan, d_stats, smem, st);
+    case 4:
+      return qg_launch_cluster_g<4>(d_insts, ninst, plan, d_stats, smem, st);
+    case 8:
+      return qg_launch_cluster_g<8>(d_insts, ninst, plan, d_stats, smem, st);
+    case 16:
+      return qg_launch_cluster_g<16>(d_insts, ninst, plan, d_stats, smem, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+size_t qg_cluster_smem(int n, int S, int G, int restart) {
+  if (G < 1 || G > 16 || (G & (G - 1)) || n % G || n / G < 8 || S < 2 || S > QG_MAX_S) return 0;
+  // local vectors of at most kClusterLocal values, split evenly into the
+  // G shares of the centre phase
+  if ((long long)S * (n / G) > qg::kClusterLocal || (S * (n / G)) % G) return 0;
+  const size_t t = qg::cluster_smem_layout(n / G, S, G, restart).total;
+  return t <= (size_t)227 * 1024 ? t : 0;
 }

@@ -171,3 +171,18 @@ def test_full_size_nai_members_implicit_equation_in_batch(qglib, cuda, precision
         Hchi = oham.apply_h_matrix_free(wl.NAI_QMIN, wl.NAI_QMAX, n, wl.NAI_REDUCED_MASS, V, F, chi)
         r = chi + 1j * tau * Hchi - psi0
         assert np.linalg.norm(r) / np.linalg.norm(psi0) < 1e-13
+
+
+@pytest.mark.parametrize("G", [4, 8])
+def test_operating_point_cluster_batch_vs_oracle(qglib, cuda, op_reference, G):
+    # the same point in the shared-memory cluster form, one launch per step
+    qg = qglib
+    grid, model, states = _op_batch(qg, qg.QG_C128)
+    batch = qg.Batch(states)
+    batch.set_cluster(G)
+    opts = _op_opts(qg)
+    for k in range(STEPS):
+        stt, stats = batch.run(qg.QG_MIDPOINT, 8, qg.QG_SUZUKI, DT_OP, 1, opts)
+        assert stt == [0] * len(SEEDS)
+        for st, want in zip(states, op_reference["after"][k]):
+            assert rel_l2(st.get(), want) < 1e-11
