@@ -241,6 +241,7 @@ def run_ours(args):
     if world > 1:
         t_ms = max_over_ranks(t_ms, "cuda")
         dist.barrier()
+    psi_after = states[0].get() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     flat = [s for st in stats_all for s in st]
     n_hpsi = sum(s["n_hpsi"] for s in flat)
     n_sub = sum(s["n_substeps"] for s in flat)
@@ -291,7 +292,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD["name"], "N": N, "S": S, "wavepackets_per_gpu": B,
                        "method": "implicit midpoint" if m == 1 else "trapezoidal",
                        "order": o, "scheme": "suzuki" if sc == 1 else "triple_jump",
-                       "dt_fs": WORKLOAD["dt_fs"], "gmres_tol": WORKLOAD["tol"], "restart": WORKLOAD["restart"],
+                       "dt_fs": WORKLOAD["dt_fs"], "solver_tol": WORKLOAD["tol"], "restart": WORKLOAD["restart"],
                        "precision": args.precision, "solver": args.solver, "guess": _guess_name(args),
                        "l2": "working set %.0f MB > L2 (129 MB): no flush needed" %
                              (B * (WORKLOAD["restart"] + 6) * len_state * 16 / 1e6)},
@@ -313,6 +314,9 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_seconds)
+            line["cpu_same_algorithm"] = cpu_same_algorithm(budget_s=args.cpu_seconds)
+            ksteps = args.warmup + args.steps
+            line["error_vs_exact"] = error_vs_exact(wl, psi_after, shard_seeds(rank, B)[0], ksteps, dt)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -359,6 +363,93 @@ def cpu_baseline(budget_s=15.0):
     return {"value": n / el, "unit": "wavepacket-steps/s", "cores": threads, "kind": "oracle",
             "sample": "1 wavepacket, %d composed steps of the workload (N=%d, order %d); one-time dense H + LU "
                       "set-up %.1f s excluded" % (n, N, order, setup)}
+
+
+_ORA = {}
+
+
+def _oracle_nai(N):
+    """The oracle's dense H of the NaI-like model on N points (cached)."""
+    if N not in _ORA:
+        import workloads as wl
+        from oracle import fields, grid as ogrid, hamiltonian as ham
+        q, dq = ogrid.points(wl.NAI_QMIN, wl.NAI_QMAX, N)
+        W, dW = wl.nai_like_diabatic(q)
+        V, F = fields.two_state(W, dW)
+        H = ham.dense_h([wl.NAI_QMIN], [wl.NAI_QMAX], [N], [wl.NAI_REDUCED_MASS], V, F)
+        _ORA[N] = dict(q=q, dq=dq, V=V, F=F, H=H)
+    return _ORA[N]
+
+
+def _exact_evolution(N):
+    from oracle import propagate as prop
+    o = _oracle_nai(N)
+    if "ev" not in o:
+        o["ev"] = prop.ExactEvolution(o["H"])
+    return o["ev"]
+
+
+def _psi0_oracle(N, seed):
+    import workloads as wl
+    from oracle import initial
+    o = _oracle_nai(N)
+    q0, p0, s0 = wl.initial_gaussian_params(seed)
+    return initial.state_on_surface(2, 1, initial.gaussian([o["q"]], [q0], [p0], [s0]))
+
+
+def error_vs_exact(wl, psi_gpu, seed, ksteps, dt):
+    """L2 error of one propagated packet against the exact evolution
+    e^{-iHt} psi0 of the same discrete H (the oracle's eigen-decomposition),
+    after the bench's ksteps composed steps; the linear extrapolation to
+    t_f = 10500 a.u. is an estimate (the per-step error of a unitary method
+    adds up roughly linearly)."""
+    N = WORKLOAD["N"]
+    t0 = time.perf_counter()
+    ex = _exact_evolution(N)(_psi0_oracle(N, seed), ksteps * dt)
+    err = float(np.linalg.norm(psi_gpu - ex) * np.sqrt(_oracle_nai(N)["dq"]))
+    nf = 10500.0 / dt
+    return {"value": err, "t_au": ksteps * dt, "composed_steps": ksteps,
+            "estimate_at_tf": err * nf / ksteps, "reference": "oracle eigen-decomposition of the dense H",
+            "host_s": time.perf_counter() - t0}
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_same_algorithm(budget_s=10.0):
+    """The same algorithm in plain C on all host cores (oracle/cpu_baseline:
+    radix-2 FFT, Lanczos, carried H psi, OpenMP over packets), on a sample of
+    the workload: one packet per core, composed steps until budget_s."""
+    from oracle import cpu_baseline as cb
+    import workloads as wl
+    N = WORKLOAD["N"]
+    o = _oracle_nai(N)
+    npk = os.cpu_count() or 1
+    psi = np.stack([_psi0_oracle(N, s) for s in range(npk)])
+    dt = WORKLOAD["dt_fs"] * FS
+    t1 = time.perf_counter()
+    n = 0
+    info = None
+    while True:
+        info = cb.propagate(psi, wl.NAI_QMIN, wl.NAI_QMAX, wl.NAI_REDUCED_MASS, o["V"], o["F"][0], WORKLOAD["order"],
+                            dt, 1, tol=WORKLOAD["tol"])
+        n += 1
+        if time.perf_counter() - t1 >= budget_s:
+            break
+    el = time.perf_counter() - t1
+    return {"value": npk * n / el, "unit": "wavepacket-steps/s", "cores": info["threads"], "nproc": os.cpu_count(),
+            "cpu": _cpu_model(), "kind": "same algorithm in C, FP64 (FFT + Lanczos, OpenMP over packets)",
+            "status": info["status"],
+            "sample": "%d packets (one per core) x %d composed steps of the workload" % (npk, n)}
 
 
 def _blas_threads():
@@ -467,7 +558,7 @@ def run_batched(args):
             "data": "synthetic (seeded avoided-crossing models)",
             "config": {"workload": BATCHED["name"], "models": nmod, "S": "2-3", "N": "256-8192 log-uniform",
                        "method": "implicit midpoint", "order": o_, "scheme": "suzuki", "dt_fs": BATCHED["dt_fs"],
-                       "gmres_tol": BATCHED["tol"], "precision": args.precision,
+                       "solver_tol": BATCHED["tol"], "precision": args.precision,
                        "launch": "one persistent launch per step, CUDA graph replay"},
             "hpsi_grid_point_applications_per_s": hpsi_pts * args.steps / (t_ms / 1e3),
             "per_instance_path": {"value": per_value, "unit": "wavepacket-steps/s", "sample_models": ns,
@@ -546,7 +637,7 @@ def run_2d(args):
             "scaling": "strong", "vs_baseline": None, "dtype": "c64 inner / f64 residual",
             "data": "synthetic (2-D two-state model)",
             "config": {"workload": "model2d_256x256_midpoint_suzuki6", "grid": list(ns), "S": 2, "order": 6,
-                       "dt_fs": 0.1, "gmres_tol": tol, "solver": args.solver, "guess": _guess_name(args),
+                       "dt_fs": 0.1, "solver_tol": tol, "solver": args.solver, "guess": _guess_name(args),
                        "launch": "one cooperative launch over all SMs"},
             "fp64_path": {"value": args.steps / (t_f / 1e3), "ms_per_step": t_f / args.steps,
                           "fp64_hpsi": res["fp64"]["stats"]["n_hpsi"]},
@@ -703,6 +794,141 @@ def run_sweep(args):
                       "precision": args.precision}), flush=True)
 
 
+def _single_cases(args):
+    ns = args.single_steps
+    return [
+        dict(name="nai_like_n1024_trapezoidal_dt0.1fs_200steps", N=1024, method=0, order=2, scheme=1, dt=0.1 * FS,
+             nsteps=200, tol=1e-12, note="the n1024 trapezoidal configuration, whole run"),
+        dict(name="nai_like_n2048_midpoint_suzuki8_dt10.25au_one_packet", N=2048, method=1, order=8, scheme=1,
+             dt=10500.0 / 1024, nsteps=ns, tol=1e-15, note="the error-1e-10 point, %d of 1024 steps to t_f" % ns),
+        dict(name="nai_like_n4096_midpoint_suzuki8_dt10.25au_one_packet", N=4096, method=1, order=8, scheme=1,
+             dt=10500.0 / 1024, nsteps=ns, tol=1e-15, note="the same point on 4096 points, %d steps" % ns),
+    ]
+
+
+def run_single(args):
+    """One wavepacket at a time (latency): the one-CTA form against the
+    shared-memory cluster form at its smallest cluster size and twice it.
+    Prints one JSON line per case with the time per elementary step, the
+    FP64 rate against the peak of the SMs the form occupies, and the
+    time to t_f = 10500 a.u. where the case is the error-1e-10 point."""
+    import torch
+    import __graft_entry__
+    import workloads as wl
+
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    import paper_1902_04661_gb300 as qg
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for case in _single_cases(args):
+        N = case["N"]
+        grid = qg.Grid([N], [wl.NAI_QMIN], [wl.NAI_QMAX])
+        W, dW = wl.nai_like_diabatic(grid.points())
+        model = qg.Model(grid, 2, [wl.NAI_REDUCED_MASS], W=W, dW=dW)
+        q0, p0, s0 = wl.initial_gaussian_params(0)
+        opts = qg.default_solver_opts(tol=case["tol"], restart=30, max_iters=600, solver=qg.QG_SOLVER_LANCZOS)
+        g0 = qg.cluster_size(N, 2)
+        forms = {}
+        for G in (0, g0, 2 * g0 if 0 < g0 < 16 else 0):
+            if G == 0 and 0 in forms:
+                continue
+            st = qg.State(model)
+            if G:
+                st.set_cluster(G)
+            st.set_gaussian(1, [q0], [p0], [s0])
+            st.propagate(case["method"], case["order"], case["scheme"], case["dt"], 1, opts)   # warm-up
+            st.set_gaussian(1, [q0], [p0], [s0])
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            stats = st.propagate(case["method"], case["order"], case["scheme"], case["dt"], case["nsteps"], opts)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            flops = _flops_per_launch([stats], N, 2)
+            used = max(1, G)
+            peak = fp64_peak_tflops() * used / sms
+            forms["cluster%d" % G if G else "one_cta"] = {
+                "ms": ms, "us_per_substep": 1e3 * ms / max(1, stats["n_substeps"]),
+                "ms_per_composed_step": ms / case["nsteps"], "sms": used,
+                "fp64_tflops": flops / (ms * 1e-3) / 1e12, "frac_of_used_sms_peak": flops / (ms * 1e-3) / 1e12 / peak,
+                "hpsi_per_substep": stats["n_hpsi"] / max(1, stats["n_substeps"]), "status": stats["status"]}
+        best = min(forms.values(), key=lambda f: f["ms"])
+        line = {"metric": "time per elementary step of one wavepacket (latency)", "value": best["us_per_substep"],
+                "unit": "us/substep", "n_gpus": 1, "steps": case["nsteps"], "warmup": 1,
+                "ms_per_step": best["ms_per_composed_step"], "higher_is_better": False, "scaling": "none",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded NaI-like model and Gaussian)",
+                "config": {"workload": case["name"], "N": N, "S": 2, "note": case["note"], "solver_tol": case["tol"]},
+                "forms": forms}
+        if case["nsteps"] != 200:
+            line["time_to_tf_s_estimate"] = best["ms_per_composed_step"] * 1024 / 1e3
+        print(json.dumps(line), flush=True)
+
+
+CONFIG2 = {
+    # (scheme, order): step counts n over t_f (dt = t_f / n)
+    (1, 8): [512, 768, 1024, 1536],
+    (2, 8): [1024, 1536, 2048, 3072, 4096],
+    (2, 6): [2048, 4096, 8192],
+    (1, 6): [2048, 4096],
+}
+
+
+def run_config2(args):
+    """Wavefunction error against the exact evolution (Sec. III, Fig. 5): the
+    NaI-like packet propagated to t_f = 10500 a.u. for each scheme, order and
+    dt, one packet per job (shared-memory cluster form), all jobs concurrent on
+    their own streams; error = ||psi_dt(t_f) - e^{-iHt_f} psi0|| with the
+    oracle's eigen-decomposition of the same dense H.  Prints one line per job
+    and, per grid, the cheapest job at error <= 1e-10."""
+    import concurrent.futures as cf
+    import torch
+    import __graft_entry__
+    import workloads as wl
+
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    import paper_1902_04661_gb300 as qg
+
+    tf = args.tf
+    for N in [int(x) for x in args.config2_n.split(",")]:
+        t0 = time.perf_counter()
+        ex = _exact_evolution(N)(_psi0_oracle(N, None), tf)
+        ref_s = time.perf_counter() - t0
+        dq = _oracle_nai(N)["dq"]
+        grid = qg.Grid([N], [wl.NAI_QMIN], [wl.NAI_QMAX])
+        W, dW = wl.nai_like_diabatic(grid.points())
+        model = qg.Model(grid, 2, [wl.NAI_REDUCED_MASS], W=W, dW=dW)
+        G = qg.cluster_size(N, 2)
+        opts = qg.default_solver_opts(tol=args.sweep_tol, restart=30, max_iters=600, solver=qg.QG_SOLVER_LANCZOS)
+        jobs = [(sc, o, n) for (sc, o), ns in CONFIG2.items() for n in ns]
+
+        def one(job):
+            scheme, order, n = job
+            stream = torch.cuda.Stream()
+            st = qg.State(model, stream=stream)
+            st.set_cluster(G)
+            st.set_gaussian(1, [wl.NAI_Q0], [wl.NAI_P0], [wl.NAI_SIGMA0])
+            t1 = time.perf_counter()
+            stats = st.propagate(WORKLOAD["method"], order, scheme, tf / n, n, opts, allow_fail=True)
+            el = time.perf_counter() - t1
+            err = float(np.linalg.norm(st.get() - ex) * np.sqrt(dq))
+            row = {"N": N, "scheme": {0: "triple_jump", 1: "suzuki", 2: "optimal"}[scheme], "order": order,
+                   "nsteps": n, "dt_au": tf / n, "status": stats["status"], "error_vs_exact": err,
+                   "wall_s": el, "hpsi": stats["n_hpsi"], "substeps": stats["n_substeps"], "cluster": G}
+            print(json.dumps(row), flush=True)
+            return row
+
+        with cf.ThreadPoolExecutor(len(jobs)) as exe:
+            rows = list(exe.map(one, jobs))
+        ok = [r for r in rows if r["status"] == 0 and r["error_vs_exact"] <= 1e-10]
+        best = min(ok, key=lambda r: r["hpsi"]) if ok else None
+        print(json.dumps({"config2_best_at_1e-10": best, "N": N, "t_f": tf, "tol": args.sweep_tol,
+                          "reference": "oracle eigen-decomposition, %.1f s on the host" % ref_s}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -718,7 +944,9 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="convergence-error sweep that fixes the operating point")
     ap.add_argument("--solver", default="lanczos", choices=["gmres", "lanczos"],
                     help="Krylov method of the implicit steps (same minimal-residual iterates)")
-    ap.add_argument("--workload", default="nai", choices=["nai", "batched", "2d", "adjoint"])
+    ap.add_argument("--workload", default="nai", choices=["nai", "batched", "2d", "adjoint", "single", "config2"])
+    ap.add_argument("--single-steps", type=int, default=16, help="composed steps of the one-packet cases")
+    ap.add_argument("--config2-n", default="2048,4096", help="grid sizes of the config2 error sweep")
     ap.add_argument("--models", type=int, default=0)
     ap.add_argument("--tol2d", type=float, default=1e-12, help="solver tolerance of the 2-D workload")
     ap.add_argument("--per-instance-sample", type=int, default=64)
@@ -737,6 +965,10 @@ def main():
         run_2d(args)
     elif args.workload == "adjoint" and args.impl == "ours":
         run_adjoint(args)
+    elif args.workload == "single" and args.impl == "ours":
+        run_single(args)
+    elif args.workload == "config2" and args.impl == "ours":
+        run_config2(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -133,6 +133,18 @@ def exact(H, psi, t):
     return (U @ (np.exp(-1j * lam * t / HBAR) * c)).reshape(psi.shape)
 
 
+class ExactEvolution:
+    """e^{-iHt/hbar} for many states and times from one Hermitian
+    eigen-decomposition of H (the same definition as exact())."""
+
+    def __init__(self, H):
+        self.lam, self.U = np.linalg.eigh(np.asarray(H, dtype=np.complex128))
+
+    def __call__(self, psi, t):
+        c = self.U.conj().T @ psi.reshape(-1)
+        return (self.U @ (np.exp(-1j * self.lam * t / HBAR) * c)).reshape(psi.shape)
+
+
 def cayley_by_eigen(H, psi, dt, fractions, nsteps=1):
     """Composed Cayley steps through the eigen-decomposition: every elementary
     step multiplies eigen-component lambda by R(f dt lambda / hbar) with

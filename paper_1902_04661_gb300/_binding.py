@@ -50,6 +50,7 @@ EXPORTED = [
     "qg_overlap", "qg_batch_propagate", "qg_batch_create", "qg_batch_run", "qg_batch_capture", "qg_batch_replay", "qg_batch_stats",
     "qg_batch_stream", "qg_batch_destroy", "qg_batch_autotune", "qg_batch_tuning", "qg_selftest_barrier_timeout", "qg_state_set_launch_width",
     "qg_state_autotune", "qg_state_set_adjoint", "qg_propagate_ex", "qg_batch_run_ex", "qg_propagate_noalloc", "qg_status_string", "qg_last_error_string", "qg_version",
+    "qg_state_set_cluster", "qg_cluster_size", "qg_batch_cluster", "qg_batch_set_cluster",
 ]
 
 

@@ -233,8 +233,12 @@ __host__ __device__ inline int count_radix8(const int* radix, int npass) {
 // the twiddle table: twp[(r - 1) m + j] = w_L^{j r}, so consecutive j (the
 // lanes of a warp) read consecutive entries.  The tables are read with
 // generic loads: they may sit in global or in shared memory.
+// src (optional): read the pass's input from src (nb unpadded vectors of
+// length n, global or shared memory) instead of buf -- the first forward pass
+// then also does the copy into shared memory.
 template <int RD, bool INV, typename C>
-__device__ __forceinline__ void fft_pass(C* gbuf, int n, int nb, int L, const C* __restrict__ twp) {
+__device__ __forceinline__ void fft_pass(C* gbuf, int n, int nb, int L, const C* __restrict__ twp,
+                                         const C* src = nullptr) {
   C* buf = in_dyn_smem(gbuf);
   const int lm = ilog2(L / RD);
   const int m = 1 << lm;
@@ -247,8 +251,13 @@ __device__ __forceinline__ void fft_pass(C* gbuf, int n, int nb, int L, const C*
     const int j = bb & (m - 1);
     const int e0 = v * n + blk * L + j;
     C x[RD];
+    if (src) {
 #pragma unroll
-    for (int r = 0; r < RD; ++r) x[r] = buf[spad<C>(e0 + r * m)];
+      for (int r = 0; r < RD; ++r) x[r] = src[e0 + r * m];
+    } else {
+#pragma unroll
+      for (int r = 0; r < RD; ++r) x[r] = buf[spad<C>(e0 + r * m)];
+    }
     if (!INV) {
       dft<RD, false>(x);
       if (j) {
@@ -295,19 +304,29 @@ __device__ __forceinline__ void fft_center(C* gbuf, int n, int nb, const R* __re
 // forward FFT, multiply by i k, inverse FFT (1/n folded into kd).
 // One out-of-line copy per precision: its call sites share the code (fewer
 // instruction-cache misses than an inlined copy at every site).
+// src (optional): take the input from src (nb unpadded vectors) instead of
+// buf; the first forward pass reads it.
 template <typename R>
-__device__ __noinline__ void spectral_derivative(typename Cx<R>::T* buf, int nb, const HOp<R>& H) {
+__device__ __noinline__ void spectral_derivative(typename Cx<R>::T* buf, int nb, const HOp<R>& H,
+                                                 const typename Cx<R>::T* src = nullptr) {
   using C = typename Cx<R>::T;
   const int n = H.n, np = H.npass, n8 = H.n8;
   const C* tw = H.tw;
   const R* kd = H.kd;
+  if (src && np == 1) {   // no twiddled pass to fuse the copy into
+    C* sb = in_dyn_smem(buf);
+    for (int i = threadIdx.x; i < nb * n; i += kThreads) sb[spad<C>(i)] = src[i];
+    __syncthreads();
+    src = nullptr;
+  }
   int L = n, off = 0;
   for (int i = 0; i < np - 1; ++i) {
     const int RD = i < n8 ? 8 : 4;
+    const C* in = i == 0 ? src : nullptr;
     if (RD == 8)
-      fft_pass<8, false>(buf, n, nb, L, tw + off);
+      fft_pass<8, false>(buf, n, nb, L, tw + off, in);
     else
-      fft_pass<4, false>(buf, n, nb, L, tw + off);
+      fft_pass<4, false>(buf, n, nb, L, tw + off, in);
     off += (RD - 1) * (L / RD);
     L /= RD;
     __syncthreads();
@@ -395,6 +414,67 @@ __device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T
     }
     __syncthreads();
   }
+}
+
+// The same H psi with U = (D + F) x kept in shared memory (sU, S n values)
+// and fewer passes: the first forward pass of each derivative reads its
+// input directly (x from global memory, U from sU), and when all surfaces fit
+// in one FFT batch the coupling pass leaves U in the FFT buffer for the second
+// derivative.  DOTS: also returns the raw sums Re<x, y> and ||y||^2 in
+// dots[0..1] (one CTA reduction).  y may alias x or z.
+template <typename R, bool DOTS>
+__device__ __forceinline__ void apply_h_staged(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
+                                               typename Cx<R>::T* sU, const typename Cx<R>::T* x,
+                                               typename Cx<R>::T* y, const typename Cx<R>::T* z, R e, R a,
+                                               typename Cx<R>::T c, R* red, R* dots) {
+  using C = typename Cx<R>::T;
+  const int n = H.n, S = H.S;
+  const int ln = ilog2(n);
+  const R* F = H.F;
+  const R* V = H.V;
+  const int nb = (S <= nb_cap) ? S : 1;
+  const bool whole = nb == S;
+  C* sb = in_dyn_smem(sbuf);
+  C* su = in_dyn_smem(sU);
+  // U = (D + F) x
+  for (int s0 = 0; s0 < S; s0 += nb) {
+    spectral_derivative<R>(sbuf, nb, H, x + (size_t)s0 * n);
+    for (int i = threadIdx.x; i < nb * n; i += kThreads) {
+      const int s = s0 + (i >> ln), j = i & (n - 1);
+      C acc = sb[spad<C>(i)];
+      for (int t = 0; t < S; ++t)
+        if (t != s) acc = caxpy_r(coupling(F, n, S, s, t, j), x[t * n + j], acc);
+      su[s * n + j] = acc;
+      if (whole) sb[spad<C>(i)] = acc;
+    }
+    __syncthreads();
+  }
+  // y = e z + a x + c (-hbar^2/2m (D + F) U + V x); the Lanczos iteration
+  // (a = 0, c = 1) skips the scalings
+  const R mh = -H.h2m;
+  const bool plain = a == (R)0 && c.x == (R)1 && c.y == (R)0;
+  R d[2] = {(R)0, (R)0};
+  for (int s0 = 0; s0 < S; s0 += nb) {
+    spectral_derivative<R>(sbuf, nb, H, whole ? nullptr : su + (size_t)s0 * n);
+    for (int i = threadIdx.x; i < nb * n; i += kThreads) {
+      const int s = s0 + (i >> ln), j = i & (n - 1);
+      C acc = sb[spad<C>(i)];
+      for (int t = 0; t < S; ++t)
+        if (t != s) acc = caxpy_r(coupling(F, n, S, s, t, j), su[t * n + j], acc);
+      const C xs = x[s * n + j];
+      const R v = __ldg(V + s * n + j);
+      const C hx = cmk<C>(fma(mh, acc.x, v * xs.x), fma(mh, acc.y, v * xs.y));
+      C out = plain ? hx : caxpy(c, hx, cmk<C>(a * xs.x, a * xs.y));
+      if (e != (R)0) out = caxpy_r(e, z[s * n + j], out);
+      y[s * n + j] = out;
+      if (DOTS) {
+        d[0] = fma(xs.x, out.x, fma(xs.y, out.y, d[0]));
+        d[1] = fma(out.x, out.x, fma(out.y, out.y, d[1]));
+      }
+    }
+    __syncthreads();
+  }
+  if (DOTS) cta_sum<2>(d, red, dots);
 }
 
 // y = (D + F) x (one half of H psi; used by the adjoint to form the field

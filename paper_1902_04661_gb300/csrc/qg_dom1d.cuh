@@ -11,18 +11,42 @@ namespace qg {
 // Dynamic shared memory of the 1-D kernels: the FFT buffer (nb_cap vectors of
 // max_n complex doubles, also used by the FP32 passes), then the GMRES arrays
 // sized for doubles (the FP32 arrays fit in the same space).
+// Optional staging regions follow (flags of the launch, see stage_plan):
+// kStageTables -- the instance's FP64 twiddles and wave numbers (max_n
+// double2 + max_n double), so the FFT passes read them from shared memory;
+// kStageU -- the intermediate U = (D + F) x of H psi (max_S x max_n double2),
+// so H psi makes fewer passes over global memory.
+enum { kStageTables = 1, kStageU = 2 };
+
 struct Smem {
   unsigned char* fft;
   unsigned char* gm;
+  double2* tw;   // staged twiddles or null
+  double* kd;    // staged wave numbers or null
+  double2* su;   // staged U or null
   int nb_cap;
   int m;
 };
 
-static __device__ Smem carve_smem(void* base, int max_n, int nb_cap, int m) {
+__host__ __device__ inline size_t gm_region_bytes(int m) { return (gmres_smem_bytes(m) + 255) & ~size_t(255); }
+
+static __device__ Smem carve_smem(void* base, int max_n, int nb_cap, int m, int stage = 0, int max_S = 0) {
   Smem s;
   unsigned char* p = reinterpret_cast<unsigned char*>(base);
   s.fft = p;
-  s.gm = p + padded_bytes((size_t)nb_cap * max_n, sizeof(double2));
+  p += (padded_bytes((size_t)nb_cap * max_n, sizeof(double2)) + 255) & ~size_t(255);
+  s.gm = p;
+  p += gm_region_bytes(m);
+  s.tw = nullptr;
+  s.kd = nullptr;
+  s.su = nullptr;
+  if (stage & kStageTables) {
+    s.tw = reinterpret_cast<double2*>(p);
+    p += (size_t)max_n * sizeof(double2);
+    s.kd = reinterpret_cast<double*>(p);
+    p += ((size_t)max_n * sizeof(double) + 255) & ~size_t(255);
+  }
+  if (stage & kStageU) s.su = reinterpret_cast<double2*>(p);
   s.nb_cap = nb_cap;
   s.m = m;
   return s;
@@ -61,8 +85,11 @@ __device__ __forceinline__ HOp<float> hop32(const InstDesc& I, float2* U) {
 
 // One CTA owns one whole 1-D instance.
 struct Dom1D {
-  static constexpr bool kFusedDots = false;   // CTA-local sums are cheap: reduce them separately
+  // with U staged in shared memory, H psi forms Re<x, y> and ||y||^2 in its
+  // last pass (hpsi with dots); without it the solvers reduce them separately
+  static constexpr bool kFusedDots = true;
   int len;
+  double2* su;    // staged U (shared memory) or null
   double dv;
   unsigned char* gm;
   double* red;
@@ -92,14 +119,48 @@ struct Dom1D {
   template <typename R>
   __device__ __forceinline__ void hpsi(const typename Cx<R>::T* x, typename Cx<R>::T* y,
                                        const typename Cx<R>::T* z, R e, R a, typename Cx<R>::T c) {
-    if constexpr (sizeof(R) == 8)
-      apply_h_axpby<double>(H64, reinterpret_cast<double2*>(fb), nb_cap, x, y, z, e, a, c);
-    else
-      apply_h_axpby<float>(H32, reinterpret_cast<float2*>(fb), 2 * nb_cap, x, y, z, e, a, c);
+    if constexpr (sizeof(R) == 8) {
+      if (su)
+        apply_h_staged<double, false>(H64, reinterpret_cast<double2*>(fb), nb_cap, su, x, y, z, e, a, c, nullptr,
+                                      nullptr);
+      else
+        apply_h_axpby<double>(H64, reinterpret_cast<double2*>(fb), nb_cap, x, y, z, e, a, c);
+    } else {
+      if (su)
+        apply_h_staged<float, false>(H32, reinterpret_cast<float2*>(fb), 2 * nb_cap, reinterpret_cast<float2*>(su),
+                                     x, y, z, e, a, c, nullptr, nullptr);
+      else
+        apply_h_axpby<float>(H32, reinterpret_cast<float2*>(fb), 2 * nb_cap, x, y, z, e, a, c);
+    }
+  }
+  // the same, also returning the raw sums Re<x, y> and ||y||^2 in dots[0..1]
+  template <typename R>
+  __device__ __forceinline__ void hpsi(const typename Cx<R>::T* x, typename Cx<R>::T* y,
+                                       const typename Cx<R>::T* z, R e, R a, typename Cx<R>::T c, R* dots) {
+    using C = typename Cx<R>::T;
+    R* rd = reinterpret_cast<R*>(red);
+    if (su) {
+      if constexpr (sizeof(R) == 8)
+        apply_h_staged<double, true>(H64, reinterpret_cast<double2*>(fb), nb_cap, su, x, y, z, e, a, c, rd, dots);
+      else
+        apply_h_staged<float, true>(H32, reinterpret_cast<float2*>(fb), 2 * nb_cap, reinterpret_cast<float2*>(su), x,
+                                    y, z, e, a, c, rd, dots);
+      return;
+    }
+    hpsi<R>(x, y, z, e, a, c);
+    R v[2] = {(R)0, (R)0};
+    each([&](int i) {
+      const C xs = x[i], out = y[i];
+      v[0] = fma(xs.x, out.x, fma(xs.y, out.y, v[0]));
+      v[1] = fma(out.x, out.x, fma(out.y, out.y, v[1]));
+    });
+    cta_sum<2>(v, rd, dots);
   }
   __device__ __forceinline__ bool ok() const { return true; }
 };
 
+// The instance's H psi operands; with kStageTables the FP64 twiddles and
+// wave numbers are first copied into shared memory.
 static __device__ Dom1D make_dom1d(const InstDesc& I, const Smem& sm, int m, double* red) {
   const int len = I.S * I.n;
   Dom1D D;
@@ -108,6 +169,16 @@ static __device__ Dom1D make_dom1d(const InstDesc& I, const Smem& sm, int m, dou
   D.gm = sm.gm;
   D.red = red;
   D.H64 = hop64(I, I.work);
+  if (sm.tw) {
+    for (int k = threadIdx.x; k < I.n; k += kThreads) {
+      sm.tw[k] = I.tw[k];
+      sm.kd[k] = I.kd[k];
+    }
+    __syncthreads();
+    D.H64.tw = sm.tw;
+    D.H64.kd = sm.kd;
+  }
+  D.su = sm.su;
   D.fb = sm.fft;
   D.nb_cap = sm.nb_cap;
   D.basis64 = I.work + (size_t)4 * len;
@@ -233,10 +304,28 @@ static __device__ void run_adjoint(const InstDesc& I, const StepPlan& P, const S
 // within `budget` bytes of dynamic shared memory; force_nb > 0 caps the count.
 static inline int nb_capacity(int max_n, int max_S, int restart, size_t* bytes_out, size_t budget = 200 * 1024,
                               int force_nb = 0) {
-  const size_t rest = qg::gmres_smem_bytes(restart);
+  const size_t rest = qg::gm_region_bytes(restart);
   int nb = max_S;
-  if (qg::padded_bytes((size_t)max_S * max_n, 16) + rest > budget) nb = 1;
+  if (((qg::padded_bytes((size_t)max_S * max_n, 16) + 255) & ~size_t(255)) + rest > budget) nb = 1;
   if (force_nb > 0 && force_nb < nb) nb = force_nb;
-  if (bytes_out) *bytes_out = qg::padded_bytes((size_t)nb * max_n, 16) + rest + 64;
+  if (bytes_out) *bytes_out = ((qg::padded_bytes((size_t)nb * max_n, 16) + 255) & ~size_t(255)) + rest + 64;
   return nb;
+}
+
+// Staging regions (qg::kStageTables, qg::kStageU) that fit after the FFT
+// buffers and GMRES arrays (*bytes, updated) within the budget: tables
+// first, then U.
+static inline int stage_plan(int max_n, int max_S, size_t budget, size_t* bytes) {
+  int stage = 0;
+  const size_t tab = (size_t)max_n * 16 + (((size_t)max_n * 8 + 255) & ~size_t(255));
+  if (*bytes + tab <= budget) {
+    stage |= qg::kStageTables;
+    *bytes += tab;
+  }
+  const size_t u = (size_t)max_S * max_n * 16;
+  if (*bytes + u <= budget) {
+    stage |= qg::kStageU;
+    *bytes += u;
+  }
+  return stage;
 }

@@ -189,14 +189,14 @@ cudaError_t qg_launch_propagate(const InstDesc* d_insts, int ninst, const StepPl
 // each); grid 0 only sets the kernel's shared-memory attribute.
 template <int MINB>
 cudaError_t qg_launch_propagate_minb(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
-                                     qg_step_stats* d_stats, int max_n, int nb, size_t smem, int grid,
-                                     cudaStream_t st);
+                                     qg_step_stats* d_stats, int max_n, int max_S, int nb, int stage, size_t smem,
+                                     int grid, cudaStream_t st);
 template <>
-cudaError_t qg_launch_propagate_minb<1>(const InstDesc*, int, const StepPlan&, int*, qg_step_stats*, int, int, size_t,
-                                        int, cudaStream_t);
+cudaError_t qg_launch_propagate_minb<1>(const InstDesc*, int, const StepPlan&, int*, qg_step_stats*, int, int, int, int,
+                                        size_t, int, cudaStream_t);
 template <>
-cudaError_t qg_launch_propagate_minb<2>(const InstDesc*, int, const StepPlan&, int*, qg_step_stats*, int, int, size_t,
-                                        int, cudaStream_t);
+cudaError_t qg_launch_propagate_minb<2>(const InstDesc*, int, const StepPlan&, int*, qg_step_stats*, int, int, int, int,
+                                        size_t, int, cudaStream_t);
 cudaError_t qg_launch_propagate_tuned(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
                                       qg_step_stats* d_stats, int max_n, int max_S, int ctas_per_sm, int nb_pref,
                                       cudaStream_t st);

@@ -254,9 +254,13 @@ cudaError_t qg_launch_propagate_tuned(const InstDesc* d_insts, int ninst, const 
   const size_t budget = ctas_per_sm >= 2 ? 110 * 1024 : 200 * 1024;
   const int nb = nb_capacity(max_n, max_S, plan.restart, &smem, budget, nb_pref);
   if (smem > budget + 1024) return cudaErrorInvalidConfiguration;
+  // staging may use what one CTA per SM leaves free (227 KB less the static
+  // arrays), or the 2-CTA budget
+  const int stage = stage_plan(max_n, max_S, ctas_per_sm >= 2 ? 110 * 1024 : 224 * 1024, &smem);
   if (ninst == 0)   // attributes only
-    return ctas_per_sm >= 2 ? qg_launch_propagate_minb<2>(d_insts, 0, plan, d_counter, d_stats, max_n, nb, smem, 0, st)
-                            : qg_launch_propagate_minb<1>(d_insts, 0, plan, d_counter, d_stats, max_n, nb, smem, 0, st);
+    return ctas_per_sm >= 2
+               ? qg_launch_propagate_minb<2>(d_insts, 0, plan, d_counter, d_stats, max_n, max_S, nb, stage, smem, 0, st)
+               : qg_launch_propagate_minb<1>(d_insts, 0, plan, d_counter, d_stats, max_n, max_S, nb, stage, smem, 0, st);
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -265,8 +269,9 @@ cudaError_t qg_launch_propagate_tuned(const InstDesc* d_insts, int ninst, const 
   cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (ctas_per_sm >= 2)
-    return qg_launch_propagate_minb<2>(d_insts, ninst, plan, d_counter, d_stats, max_n, nb, smem, grid, st);
-  return qg_launch_propagate_minb<1>(d_insts, ninst, plan, d_counter, d_stats, max_n, nb, smem, grid, st);
+    return qg_launch_propagate_minb<2>(d_insts, ninst, plan, d_counter, d_stats, max_n, max_S, nb, stage, smem, grid,
+                                       st);
+  return qg_launch_propagate_minb<1>(d_insts, ninst, plan, d_counter, d_stats, max_n, max_S, nb, stage, smem, grid, st);
 }
 
 cudaError_t qg_launch_propagate(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,

@@ -17,12 +17,12 @@ namespace qg {
 template <int MINB>
 __global__ void __launch_bounds__(QG_THREADS, MINB)
     propagate_kernel(const InstDesc* __restrict__ insts, int ninst, const StepPlan P, int* counter,
-                     qg_step_stats* stats, int max_n, int nb_cap) {
+                     qg_step_stats* stats, int max_n, int max_S, int nb_cap, int stage) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ double red[kWarps * 16];
   __shared__ double sc[64];
   __shared__ int s_idx;
-  const Smem sm = carve_smem(dyn, max_n, nb_cap, P.restart);
+  const Smem sm = carve_smem(dyn, max_n, nb_cap, P.restart, stage, max_S);
   for (int guard = 0; guard < ninst + 1; ++guard) {
     if (threadIdx.x == 0) s_idx = atomicAdd(counter, 1);
     __syncthreads();
@@ -41,11 +41,12 @@ __global__ void __launch_bounds__(QG_THREADS, MINB)
 
 template <>
 cudaError_t qg_launch_propagate_minb<QG_MINB>(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
-                                              qg_step_stats* d_stats, int max_n, int nb, size_t smem, int grid,
-                                              cudaStream_t st) {
+                                              qg_step_stats* d_stats, int max_n, int max_S, int nb, int stage,
+                                              size_t smem, int grid, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(qg::propagate_kernel<QG_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess || grid == 0) return e;   // grid 0: attributes only
-  qg::propagate_kernel<QG_MINB><<<grid, QG_THREADS, smem, st>>>(d_insts, ninst, plan, d_counter, d_stats, max_n, nb);
+  qg::propagate_kernel<QG_MINB><<<grid, QG_THREADS, smem, st>>>(d_insts, ninst, plan, d_counter, d_stats, max_n,
+                                                                 max_S, nb, stage);
   return cudaGetLastError();
 }

@@ -97,3 +97,9 @@ def test_columns_route_equals_one_state_route(small, method):
     for got, psi in zip(many, (small["psi"], small["phi"])):
         want = st.propagate(psi, 30.0, 2, method, 6, comp.SUZUKI)
         assert np.linalg.norm(got - want) < 1e-12
+
+
+def test_cached_exact_evolution_equals_exact(small):
+    ev = prop.ExactEvolution(small["H"])
+    for t in (0.0, 37.5, -120.0):
+        assert np.linalg.norm(ev(small["psi"], t) - prop.exact(small["H"], small["psi"], t)) < 1e-12
