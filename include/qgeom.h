@@ -204,6 +204,27 @@ qg_status qg_create_model(qg_grid_t g, int S, const double* mass, const double* 
  * component positive at the first point).  Only D = 1 grids. */
 qg_status qg_create_model_diabatic(qg_grid_t g, int S, const double* mass, const double* W,
                                    const double* dW, int on_device, qg_model_t* out);
+/* Model in the diabatic representation (Sec. II E):
+ *     H_diab = 1/2 p^T m^{-1} p 1 + W(q),
+ * no vector coupling; W is the real symmetric diabatic matrix in the upper-
+ * triangle layout above (S(S+1)/2 * N doubles).  H psi takes 2 transforms per
+ * surface (the second derivative) and the pointwise W; all propagation
+ * methods, solvers and the mixed precision form apply.  Only D = 1 grids; not
+ * available in the cluster form, adjoint runs or qg_propagate_noalloc.
+ * qg_model_fields returns V = the diagonal of W and F = its upper triangle. */
+qg_status qg_create_model_diabatic_rep(qg_grid_t g, int S, const double* mass, const double* W, int on_device,
+                                       qg_model_t* out);
+/* Changes of representation with the O(q) of an adiabatic model built by
+ * qg_create_model_diabatic (D = 1): psi = O(q)^T psi_diab (Eq.
+ * psi_diab2adiab) and its inverse psi_diab = O(q) psi.  O's columns are the
+ * adiabatic states in ascending order -- for S = 2 the paper's closed form
+ * (Eq. ..._orthogonal_transformation) with its columns swapped, for S >= 3 the
+ * sign-continuous eigenvectors -- consistent with the model's F = O^T O'.
+ * Buffers are S * N complex128 (host or device per on_device; may be the
+ * same buffer); synchronous.  QG_ERR_UNSUPPORTED for models without O. */
+qg_status qg_diabatic_to_adiabatic(qg_model_t m, const void* psi_diab, void* psi_adiab, int on_device);
+qg_status qg_adiabatic_to_diabatic(qg_model_t m, const void* psi_adiab, void* psi_diab, int on_device);
+
 /* Copy the model's V and F (layouts above) to host (on_device = 0) or device
  * buffers. */
 qg_status qg_model_fields(qg_model_t m, double* V, double* F, int on_device);
@@ -247,6 +268,15 @@ qg_status qg_get_state(qg_state_t s, void* psi, int on_device);
  * normalised on the grid.  q0, p0, sigma0: D entries each. */
 qg_status qg_set_gaussian(qg_state_t s, int surface, const double* q0, const double* p0,
                           const double* sigma0);
+
+/* Trigonometric interpolation (Appendix B compares wavepackets on grids of
+ * different density this way): dst's state becomes the trigonometric
+ * interpolant of src's state, p(q) = (1/N) sum_k c_k exp(i k (q - qmin)),
+ * c the DFT of src's samples, the Nyquist term a cosine, evaluated at dst's
+ * grid points; points of dst outside src's interval see the periodic
+ * extension.  Both 1-D with the same S; the grids may differ in N and range.
+ * O(N_src (N_src + N_dst)) direct sums on the device; synchronous. */
+qg_status qg_interpolate(qg_state_t src, qg_state_t dst);
 
 /* out = H psi (Eq. adiab_mol_ham by the dynamic Fourier method, Sec. II D);
  * out: S * prod(N_d) complex128, host or device per on_device. */
@@ -334,22 +364,30 @@ qg_status qg_batch_run(qg_batch_t b, int method, int order, int scheme, double d
 qg_status qg_batch_capture(qg_batch_t b, int method, int order, int scheme, double dt, int64_t nsteps,
                            const qg_solver_opts* opts);
 qg_status qg_batch_replay(qg_batch_t b);
-/* Autotuner of the batched launch (not in the paper): times trial_steps
- * composed steps of the real batch under each candidate launch shape --
- * {1, 2} CTAs per SM x {all surfaces of an instance per shared-memory FFT
- * batch, one surface at a time} for the one-CTA form, then the shared-memory
- * cluster form (see qg_state_set_cluster) at the smallest cluster size that
- * holds every instance and at twice that size -- restoring every state after
- * each trial, and keeps the fastest for later qg_batch_run /
- * qg_batch_capture calls (a captured graph is dropped).  ms_out (6 doubles,
- * may be NULL) receives the trial times in that order, -1 for a shape that
- * does not fit.  qg_batch_tuning reports the chosen one-CTA shape
- * (surfaces_per_fft 0 = all), qg_batch_cluster the chosen cluster size (0 =
- * the one-CTA form); qg_batch_set_cluster sets it by hand. */
+/* Autotuner of the batched launch (not in the paper).  A batch is split into
+ * grid-size classes (instances of equal N; largest N first), each run as its
+ * own persistent launch in the batch's stream, one after another.  For every
+ * class the autotuner times trial_steps composed steps of the class's
+ * instances under each candidate launch shape -- {1, 2} CTAs per SM x {all
+ * surfaces of an instance per shared-memory FFT batch, one surface at a time}
+ * for the one-CTA form, then the shared-memory cluster form (see
+ * qg_state_set_cluster) at the smallest cluster size that holds the class
+ * and at twice that size -- restoring the states after each trial, and keeps
+ * the fastest shape per class for later qg_batch_run / qg_batch_capture
+ * calls (a captured graph is dropped).  ms_out (6 doubles, may be NULL)
+ * receives the trial times of the first class (the largest grid) in that
+ * order, -1 for a shape that does not fit.  qg_batch_tuning reports the
+ * first class's one-CTA shape (surfaces_per_fft 0 = all), qg_batch_cluster
+ * its cluster size (0 = the one-CTA form); qg_batch_classes reports every
+ * class (arrays of up to 12 entries, any may be NULL): grid size, instance
+ * count and chosen shape.  qg_batch_set_cluster sets the cluster form for
+ * every class by hand (QG_ERR_UNSUPPORTED if a class does not fit it). */
 qg_status qg_batch_autotune(qg_batch_t b, int method, int order, int scheme, double dt, int64_t trial_steps,
                             const qg_solver_opts* opts, double* ms_out);
 qg_status qg_batch_tuning(qg_batch_t b, int* ctas_per_sm, int* surfaces_per_fft);
 qg_status qg_batch_cluster(qg_batch_t b, int* G);
+qg_status qg_batch_classes(qg_batch_t b, int* nclass, int* grid_n, int* count, int* ctas_per_sm,
+                           int* surfaces_per_fft, int* cluster);
 qg_status qg_batch_set_cluster(qg_batch_t b, int G);
 qg_status qg_batch_stats(qg_batch_t b, int32_t* statuses, qg_step_stats* stats);
 void* qg_batch_stream(qg_batch_t b);

@@ -21,6 +21,10 @@ in the paper's notation with dense matrices:
                      imp_midpoint) with dense LU solves, compositions
 * observables.py  -- inner product, norm, populations, energy, symplectic form
                      (Sec. II A)
+* representation.py -- diabatic Hamiltonian, psi = O^T psi_diab (Sec. II E),
+                     trigonometric interpolation between grids (Appendix B)
+* cpu_baseline/   -- the same algorithm as the GPU library in plain C with
+                     OpenMP (a timing baseline, pinned to the dense oracle)
 
 Conventions (the paper leaves them open; each is a stated reading):
 hbar = 1; grid q_j = qmin + j*dq, dq = (qmax - qmin)/N, periodic;
@@ -29,4 +33,4 @@ k_j = 2 pi/(N dq) * (j if j < N/2 else j - N); inner product
 adiabatic surfaces in ascending energy (index 0 = ground);
 state layout (S, N_1, ..., N_D), C order.
 """
-from . import composition, grid, hamiltonian, fields, initial, propagate, observables  # noqa: F401
+from . import composition, grid, hamiltonian, fields, initial, propagate, observables, representation  # noqa: F401

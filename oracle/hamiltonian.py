@@ -110,3 +110,42 @@ def apply_h_matrix_free(qmin, qmax, n, mass, V, F_upper, psi):
             acc = acc + np.conj(-1j * HBAR) * Ff[t, s] * Apsi[t]
         out[s] = acc / (2.0 * mass) + V[s] * psi[s]
     return out
+
+
+def _circulant_along(d, x, axis, adjoint=False):
+    """Apply the circulant derivative with first column d along one axis of x
+    (explicit sums, line by line)."""
+    x = np.moveaxis(np.asarray(x, dtype=np.complex128), axis, -1)
+    out = np.empty_like(x)
+    flat_in = x.reshape(-1, x.shape[-1])
+    flat_out = out.reshape(-1, x.shape[-1])
+    for r in range(flat_in.shape[0]):
+        flat_out[r] = _circulant_apply(d, flat_in[r], adjoint=adjoint)
+    return np.moveaxis(out, -1, axis)
+
+
+def apply_h_matrix_free_2d(qmins, qmaxs, ns, masses, V, F_upper, psi):
+    """H psi on a 2-D grid without forming H:
+    H = sum_d (1/2 m_d) A_d^H A_d + V,  A_d = p_d - i hbar F_d,  p_d = -i hbar D_d,
+    D_d the circulant spectral derivative along axis d (explicit sums), the
+    conjugate transposes taken literally.  V: (S, n0, n1); F_upper:
+    (2, S(S-1)/2, n0, n1); psi: (S, n0, n1)."""
+    V = np.asarray(V, dtype=np.float64)
+    S = V.shape[0]
+    Ff = coupling_full(F_upper, S)                # (2, S, S, n0, n1)
+    psi = np.asarray(psi, dtype=np.complex128).reshape((S,) + tuple(ns))
+    out = V * psi
+    for ax in range(2):
+        dker = _derivative_kernel(qmins[ax], qmaxs[ax], ns[ax])
+        A = np.empty_like(psi)
+        for s in range(S):
+            acc = -1j * HBAR * _circulant_along(dker, psi[s], ax)
+            for t in range(S):
+                acc = acc - 1j * HBAR * Ff[ax, s, t] * psi[t]
+            A[s] = acc
+        for s in range(S):
+            acc = np.conj(-1j * HBAR) * _circulant_along(dker, A[s], ax, adjoint=True)
+            for t in range(S):
+                acc = acc + np.conj(-1j * HBAR) * Ff[ax, t, s] * A[t]
+            out[s] = out[s] + acc / (2.0 * masses[ax])
+    return out

@@ -51,6 +51,8 @@ EXPORTED = [
     "qg_batch_stream", "qg_batch_destroy", "qg_batch_autotune", "qg_batch_tuning", "qg_selftest_barrier_timeout", "qg_state_set_launch_width",
     "qg_state_autotune", "qg_state_set_adjoint", "qg_propagate_ex", "qg_batch_run_ex", "qg_propagate_noalloc", "qg_status_string", "qg_last_error_string", "qg_version",
     "qg_state_set_cluster", "qg_cluster_size", "qg_batch_cluster", "qg_batch_set_cluster",
+    "qg_create_model_diabatic_rep", "qg_diabatic_to_adiabatic", "qg_adiabatic_to_diabatic", "qg_interpolate",
+    "qg_batch_classes",
 ]
 
 
@@ -131,6 +133,11 @@ def lib():
             "qg_selftest_barrier_timeout": (I, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
             "qg_state_set_launch_width": (I, [P, I]),
             "qg_state_set_cluster": (I, [P, I]),
+            "qg_create_model_diabatic_rep": (I, [P, I, ctypes.POINTER(D), P, I, PP]),
+            "qg_diabatic_to_adiabatic": (I, [P, P, P, I]),
+            "qg_adiabatic_to_diabatic": (I, [P, P, P, I]),
+            "qg_interpolate": (I, [P, P]),
+            "qg_batch_classes": (I, [P, ctypes.POINTER(I)] + [ctypes.POINTER(I)] * 5),
             "qg_cluster_size": (I, [I, I, I]),
             "qg_batch_cluster": (I, [P, ctypes.POINTER(ctypes.c_int)]),
             "qg_batch_set_cluster": (I, [P, I]),
@@ -253,14 +260,42 @@ class Grid:
 
 
 class Model:
-    def __init__(self, grid, S, mass, V=None, F=None, W=None, dW=None):
+    """Adiabatic model from V, F or from a diabatic W with dW (Sec. II E), or,
+    with representation="diabatic", the diabatic-representation model of W."""
+
+    def __init__(self, grid, S, mass, V=None, F=None, W=None, dW=None, representation="adiabatic"):
         self.grid = grid
         self.S = int(S)
         self.mass = [float(m) for m in mass]
-        if W is not None:
+        self.representation = representation
+        if representation == "diabatic":
+            h = ctypes.c_void_p()
+            pw, dw, kw = _host_or_device(W, np.float64)
+            _check(lib().qg_create_model_diabatic_rep(grid.handle, self.S, _dbl_array(self.mass), pw, dw,
+                                                      ctypes.byref(h)), "qg_create_model_diabatic_rep")
+            self.handle = h
+        elif W is not None:
             self.handle = qg_create_model_diabatic(grid.handle, self.S, self.mass, W, dW)
         else:
             self.handle = qg_create_model(grid.handle, self.S, self.mass, V, F)
+
+    def _rotate(self, psi, fn):
+        shape = (self.S,) + tuple(self.grid.N)
+        p, dev, keep = _host_or_device(psi, np.complex128)
+        if dev:
+            out = psi.new_empty(psi.shape)
+        else:
+            out = np.empty(shape, dtype=np.complex128)
+        q, dq_, kq = _host_or_device(out, np.complex128)
+        _check(getattr(lib(), fn)(self.handle, p, q, dev), fn)
+        return out
+
+    def to_adiabatic(self, psi_diab):
+        """psi = O(q)^T psi_diab (Eq. psi_diab2adiab); models built from W."""
+        return self._rotate(psi_diab, "qg_diabatic_to_adiabatic")
+
+    def to_diabatic(self, psi_adiab):
+        return self._rotate(psi_adiab, "qg_adiabatic_to_diabatic")
 
     def fields(self):
         g = self.grid
@@ -329,6 +364,11 @@ class State:
     def set_launch_width(self, ctas):
         """2-D states: CTAs of the cooperative launch (0 = automatic)."""
         _check(lib().qg_state_set_launch_width(self.handle, int(ctas)), "qg_state_set_launch_width")
+
+    def interpolate_from(self, other):
+        """This state becomes the trigonometric interpolant of other's state
+        on this state's grid (Appendix B)."""
+        _check(lib().qg_interpolate(other.handle, self.handle), "qg_interpolate")
 
     def set_cluster(self, G):
         """1-D states: G = 0 one CTA with vectors in global memory; G = 1, 2,
@@ -428,7 +468,16 @@ class Batch:
                                        ctypes.byref(o), ms), "qg_batch_autotune")
         c, s = ctypes.c_int(), ctypes.c_int()
         _check(lib().qg_batch_tuning(self.handle, ctypes.byref(c), ctypes.byref(s)), "qg_batch_tuning")
-        return {"trial_ms": list(ms), "ctas_per_sm": c.value, "surfaces_per_fft": s.value, "cluster": self.cluster}
+        return {"trial_ms": list(ms), "ctas_per_sm": c.value, "surfaces_per_fft": s.value, "cluster": self.cluster,
+                "classes": self.classes()}
+
+    def classes(self):
+        """Grid-size classes of the batch with their launch shapes."""
+        nc = ctypes.c_int()
+        arr = [(ctypes.c_int * 12)() for _ in range(5)]
+        _check(lib().qg_batch_classes(self.handle, ctypes.byref(nc), *arr), "qg_batch_classes")
+        keys = ["N", "count", "ctas_per_sm", "surfaces_per_fft", "cluster"]
+        return [{k: a[c] for k, a in zip(keys, arr)} for c in range(nc.value)]
 
     @property
     def cluster(self):

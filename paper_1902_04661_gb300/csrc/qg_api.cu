@@ -234,6 +234,7 @@ InstDesc make_desc(const qg_state* s) {
   d.V32 = m->d_V32;
   d.F32 = m->d_F32;
   d.work32 = s->d_work32;
+  d.rep = m->rep;
   d.ckpt = s->adj.ckpt;
   d.nckpt = s->adj.nckpt;
   d.every = s->adj.every > 0 ? s->adj.every : 1;
@@ -469,25 +470,121 @@ qg_status qg_create_model_diabatic(qg_grid_t g, int S, const double* mass, const
   }
   const double* w = on_device ? W : dWd;
   const double* dw = on_device ? dW : ddW;
+  // O(q) is kept for the changes of representation (Eq. psi_diab2adiab)
+  if (e == cudaSuccess) e = cudaMalloc(&dvec, sizeof(double) * (size_t)S * S * n);
   if (e == cudaSuccess) {
-    if (S == 2) {
-      e = qg_launch_fields2(w, dw, n, g->D, m->d_V, m->d_F, 0);
-    } else {
-      e = cudaMalloc(&dvec, sizeof(double) * (size_t)S * S * n);
-      if (e == cudaSuccess) e = qg_launch_fieldsS(w, dw, n, S, m->d_V, m->d_F, dvec, 0);
-    }
+    if (S == 2)
+      e = qg_launch_fields2(w, dw, n, g->D, m->d_V, m->d_F, dvec, 0);
+    else
+      e = qg_launch_fieldsS(w, dw, n, S, m->d_V, m->d_F, dvec, 0);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = finish_model(m);
   if (dWd) cudaFree(dWd);
   if (ddW) cudaFree(ddW);
-  if (dvec) cudaFree(dvec);
+  if (e == cudaSuccess) {
+    m->d_O = dvec;
+  } else if (dvec) {
+    cudaFree(dvec);
+  }
   if (e != cudaSuccess) {
     set_err("qg_create_model_diabatic", e);
     qg_destroy_model(m);
     return QG_ERR_CUDA;
   }
   *out = m;
+  return QG_OK;
+}
+
+qg_status qg_create_model_diabatic_rep(qg_grid_t g, int S, const double* mass, const double* W, int on_device,
+                                       qg_model_t* out) {
+  if (!out || !W) return QG_ERR_INVALID_ARG;
+  if (g && g->D != 1) return QG_ERR_UNSUPPORTED;
+  qg_model* m;
+  qg_status st = alloc_model(g, S, mass, &m);
+  if (st != QG_OK) return st;
+  const int n = g->ntot;
+  const size_t nw = (size_t)(S * (S + 1) / 2) * n;
+  double* dWd = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    e = cudaMalloc(&dWd, sizeof(double) * nw);
+    if (e == cudaSuccess) e = cudaMemcpy(dWd, W, sizeof(double) * nw, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = qg_launch_diabatic_fields(on_device ? W : dWd, n, S, m->d_V, m->d_F, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = finish_model(m);
+  if (dWd) cudaFree(dWd);
+  if (e != cudaSuccess) {
+    set_err("qg_create_model_diabatic_rep", e);
+    qg_destroy_model(m);
+    return QG_ERR_CUDA;
+  }
+  m->rep = 1;
+  *out = m;
+  return QG_OK;
+}
+
+static qg_status rotate_state(qg_model_t m, const void* in, void* out, int on_device, int to_adiabatic) {
+  if (!m || !in || !out) return QG_ERR_INVALID_ARG;
+  if (!m->d_O || m->g->D != 1) return QG_ERR_UNSUPPORTED;
+  const int n = m->g->ntot, S = m->S;
+  const size_t bytes = sizeof(double2) * (size_t)S * n;
+  double2 *di = nullptr, *dout = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    e = cudaMalloc(&di, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(di, in, bytes, cudaMemcpyHostToDevice);
+  }
+  const double2* src = on_device ? (const double2*)in : di;
+  double2* dst = on_device ? (double2*)out : dout;
+  double2* tmp = nullptr;
+  if (e == cudaSuccess && on_device && src == dst) {   // in place: rotate into a copy
+    e = cudaMalloc(&tmp, bytes);
+    if (e == cudaSuccess) dst = tmp;
+  }
+  if (e == cudaSuccess) e = qg_launch_rotate(m->d_O, src, dst, n, S, to_adiabatic, 0);
+  if (e == cudaSuccess && tmp) e = cudaMemcpy(out, tmp, bytes, cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess && !on_device) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (di) cudaFree(di);
+  if (dout) cudaFree(dout);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) {
+    set_err("representation change", e);
+    return QG_ERR_CUDA;
+  }
+  return QG_OK;
+}
+
+qg_status qg_diabatic_to_adiabatic(qg_model_t m, const void* psi_diab, void* psi_adiab, int on_device) {
+  return rotate_state(m, psi_diab, psi_adiab, on_device, 1);
+}
+
+qg_status qg_adiabatic_to_diabatic(qg_model_t m, const void* psi_adiab, void* psi_diab, int on_device) {
+  return rotate_state(m, psi_adiab, psi_diab, on_device, 0);
+}
+
+qg_status qg_interpolate(qg_state_t src, qg_state_t dst) {
+  if (!src || !dst) return QG_ERR_INVALID_ARG;
+  const qg_grid* gs = src->m->g;
+  const qg_grid* gd = dst->m->g;
+  if (gs->D != 1 || gd->D != 1) return QG_ERR_UNSUPPORTED;
+  if (src->m->S != dst->m->S) return QG_ERR_INVALID_ARG;
+  const int S = src->m->S;
+  double2* coef = nullptr;
+  cudaError_t e = cudaStreamSynchronize(src->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&coef, sizeof(double2) * (size_t)S * gs->n[0]);
+  if (e == cudaSuccess)
+    e = qg_launch_interpolate(src->d_psi, gs->n[0], gs->qmin[0], gs->qmax[0] - gs->qmin[0], coef, dst->d_psi,
+                              gd->n[0], gd->qmin[0], gd->dq[0], S, dst->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(dst->stream);
+  if (coef) cudaFree(coef);
+  if (e != cudaSuccess) {
+    set_err("qg_interpolate", e);
+    return QG_ERR_CUDA;
+  }
   return QG_OK;
 }
 
@@ -507,6 +604,7 @@ void qg_destroy_model(qg_model_t m) {
   if (m->d_F) cudaFree(m->d_F);
   if (m->d_V32) cudaFree(m->d_V32);
   if (m->d_F32) cudaFree(m->d_F32);
+  if (m->d_O) cudaFree(m->d_O);
   delete m;
 }
 
@@ -570,7 +668,7 @@ qg_status qg_state_set_cluster(qg_state_t s, int G) {
   if (!s || G < 0) return QG_ERR_INVALID_ARG;
   if (G > 0) {
     const qg_grid* g = s->m->g;
-    if (g->D != 1 || s->precision != QG_C128) return QG_ERR_UNSUPPORTED;
+    if (g->D != 1 || s->precision != QG_C128 || s->m->rep) return QG_ERR_UNSUPPORTED;
     if (qg_cluster_smem(g->n[0], s->m->S, G, 4) == 0) return QG_ERR_UNSUPPORTED;
   }
   s->cluster = G;
@@ -727,7 +825,7 @@ static qg_status check_run(int run, const StepPlan& P, const qg_state* s) {
   if (run == QG_RUN_CHECKPOINT && (!s->adj.ckpt || s->adj.every < 1 || s->adj.nckpt < 1)) return QG_ERR_INVALID_ARG;
   if (run == QG_RUN_ADJOINT &&
       (!s->adj.grad || !s->adj.gV || !s->adj.gF || P.restart > QG_MAX_RESTART - 4 || s->adj.every < 1 ||
-       P.method >= QG_EXPLICIT_EULER))
+       P.method >= QG_EXPLICIT_EULER || s->m->rep))
     return QG_ERR_INVALID_ARG;
   return QG_OK;
 }
@@ -812,8 +910,6 @@ qg_status qg_batch_create(qg_state_t* states, int nstates, qg_batch_t* out) {
   memset(b, 0, sizeof(*b));
   b->n = nstates;
   b->stream = states[0]->stream;
-  b->ctas_per_sm = 1;
-  b->nb_pref = 0;
   b->order = new (std::nothrow) int[nstates];
   if (!b->order) {
     delete b;
@@ -822,15 +918,14 @@ qg_status qg_batch_create(qg_state_t* states, int nstates, qg_batch_t* out) {
   std::vector<InstDesc> descs(nstates);
   std::vector<double> cost(nstates);
   b->all_fp64 = 1;
-  b->min_n = 1 << 30;
+  std::vector<int> ns(nstates), ss(nstates);
   for (int i = 0; i < nstates; ++i) {
     const InstDesc d = make_desc(states[i]);
     if (d.n > b->max_n) b->max_n = d.n;
     if (d.S > b->max_S) b->max_S = d.S;
-    if (d.n < b->min_n) b->min_n = d.n;
-    if (d.S * d.n > b->max_len) b->max_len = d.S * d.n;
-    if (d.precision != QG_C128) b->all_fp64 = 0;
-    b->nmask[d.S] |= 1u << ilog2h(d.n);
+    if (d.precision != QG_C128 || d.rep) b->all_fp64 = 0;   // the cluster form is adiabatic FP64 only
+    ns[i] = d.n;
+    ss[i] = d.S;
     // work estimate of one H psi: S transforms of n log2 n
     cost[i] = (double)d.S * d.n * (ilog2h(d.n) + 1);
     b->order[i] = i;
@@ -838,10 +933,38 @@ qg_status qg_batch_create(qg_state_t* states, int nstates, qg_batch_t* out) {
   b->adjoint_ready = true;
   for (int i = 0; i < nstates; ++i) {
     const qg_state_adjoint& ad = states[i]->adj;
-    if (!ad.grad || !ad.gV || !ad.gF || !ad.ckpt || ad.nckpt < 1 || ad.every < 1) b->adjoint_ready = false;
+    if (!ad.grad || !ad.gV || !ad.gF || !ad.ckpt || ad.nckpt < 1 || ad.every < 1 || states[i]->m->rep)
+      b->adjoint_ready = false;
   }
-  // longest estimated work first, so the persistent CTAs finish together
-  std::stable_sort(b->order, b->order + nstates, [&](int x, int y) { return cost[x] > cost[y]; });
+  // grid-size classes, largest N first; within a class longest estimated
+  // work first, so the persistent CTAs of a class launch finish together
+  std::stable_sort(b->order, b->order + nstates, [&](int x, int y) {
+    if (ns[x] != ns[y]) return ns[x] > ns[y];
+    return cost[x] > cost[y];
+  });
+  b->nclass = 0;
+  for (int k = 0; k < nstates; ++k) {
+    const int i = b->order[k];
+    const int c = b->nclass;
+    if (k == 0 || ns[i] != b->cls_n[c - 1]) {
+      if (c == QG_MAX_CLASSES) {
+        delete[] b->order;
+        delete b;
+        return QG_ERR_UNSUPPORTED;
+      }
+      b->cls_start[c] = k;
+      b->cls_count[c] = 0;
+      b->cls_n[c] = ns[i];
+      b->cls_S[c] = 0;
+      b->cls_ctas[c] = 1;
+      b->cls_nb[c] = 0;
+      b->cls_cluster[c] = 0;
+      b->nclass++;
+    }
+    const int cc = b->nclass - 1;
+    b->cls_count[cc]++;
+    if (ss[i] > b->cls_S[cc]) b->cls_S[cc] = ss[i];
+  }
   for (int k = 0; k < nstates; ++k) descs[k] = make_desc(states[b->order[k]]);
   cudaError_t e = cudaSuccess;
   if (b->stream == 0) {
@@ -850,7 +973,7 @@ qg_status qg_batch_create(qg_state_t* states, int nstates, qg_batch_t* out) {
   }
   if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, sizeof(InstDesc) * nstates);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_stats, sizeof(qg_step_stats) * nstates);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int) * QG_MAX_CLASSES);
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_stats, sizeof(qg_step_stats) * nstates);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, descs.data(), sizeof(InstDesc) * nstates, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -887,31 +1010,43 @@ static qg_status batch_collect(qg_batch_t b, int32_t* statuses, qg_step_stats* s
   return ret;
 }
 
-// Largest dynamic shared memory any instance of the batch needs in the
-// cluster form of size G (0 if one does not fit).
-static size_t batch_cluster_smem(const qg_batch* b, int G, int restart) {
+// Dynamic shared memory of class c in the cluster form of size G (0 if an
+// instance of the class does not fit).
+static size_t class_cluster_smem(const qg_batch* b, int c, int G, int restart) {
   if (!b->all_fp64) return 0;
   size_t best = 0;
-  for (int S = 2; S <= QG_MAX_S; ++S)
-    for (int k = 0; k < 31; ++k)
-      if (b->nmask[S] & (1u << k)) {
-        const size_t t = qg_cluster_smem(1 << k, S, G, restart);
-        if (t == 0) return 0;
-        best = std::max(best, t);
-      }
+  for (int S = 2; S <= b->cls_S[c]; ++S) {
+    const size_t t = qg_cluster_smem(b->cls_n[c], S, G, restart);
+    if (t == 0) return 0;
+    best = std::max(best, t);
+  }
   return best;
 }
 
-// One persistent launch of the batch in its current launch shape: the
-// cluster form for forward runs when chosen, else the one-CTA form.
-static cudaError_t batch_launch(qg_batch* b, const StepPlan& P, int ninst, int cluster, int ctas_per_sm, int nb_pref) {
+// The persistent launch of one class with a given shape (the cluster form
+// for forward runs when cluster > 0, else the one-CTA form).  ninst = 0 only
+// sets function attributes.
+static cudaError_t class_launch(qg_batch* b, int c, const StepPlan& P, bool all, int ctas_per_sm, int nb_pref,
+                                int cluster) {
+  const InstDesc* d = b->d_desc + b->cls_start[c];
+  qg_step_stats* st = b->d_stats + b->cls_start[c];
+  const int ninst = all ? b->cls_count[c] : 0;
   if (cluster > 0 && P.run == QG_RUN_FORWARD) {
-    const size_t smem = batch_cluster_smem(b, cluster, P.restart);
+    const size_t smem = class_cluster_smem(b, c, cluster, P.restart);
     if (smem == 0) return cudaErrorInvalidConfiguration;
-    return qg_launch_cluster(cluster, b->d_desc, ninst, P, b->d_stats, smem, b->stream);
+    return qg_launch_cluster(cluster, d, ninst, P, st, smem, b->stream);
   }
-  return qg_launch_propagate_tuned(b->d_desc, ninst, P, b->d_counter, b->d_stats, b->max_n, b->max_S, ctas_per_sm,
-                                   nb_pref, b->stream);
+  return qg_launch_propagate_tuned(d, ninst, P, b->d_counter + c, st, b->cls_n[c], b->cls_S[c], ctas_per_sm, nb_pref,
+                                   b->stream);
+}
+
+// Every class, one persistent launch each, in the batch's stream.
+static cudaError_t batch_launch(qg_batch* b, const StepPlan& P, bool all) {
+  for (int c = 0; c < b->nclass; ++c) {
+    const cudaError_t e = class_launch(b, c, P, all, b->cls_ctas[c], b->cls_nb[c], b->cls_cluster[c]);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 qg_status qg_batch_run(qg_batch_t b, int method, int order, int scheme, double dt, int64_t nsteps,
@@ -920,7 +1055,7 @@ qg_status qg_batch_run(qg_batch_t b, int method, int order, int scheme, double d
   StepPlan P;
   qg_status st = build_plan(method, order, scheme, dt, nsteps, opts, &P);
   if (st != QG_OK) return st;
-  QG_TRY(batch_launch(b, P, b->n, b->cluster, b->ctas_per_sm, b->nb_pref));
+  QG_TRY(batch_launch(b, P, true));
   return batch_collect(b, statuses, stats);
 }
 
@@ -934,7 +1069,7 @@ qg_status qg_batch_run_ex(qg_batch_t b, int run, int method, int order, int sche
   if (run == QG_RUN_ADJOINT && P.restart > QG_MAX_RESTART - 4) return QG_ERR_INVALID_ARG;
   if (run != QG_RUN_FORWARD && !b->adjoint_ready) return QG_ERR_INVALID_ARG;
   P.run = run;
-  QG_TRY(batch_launch(b, P, b->n, b->cluster, b->ctas_per_sm, b->nb_pref));
+  QG_TRY(batch_launch(b, P, true));
   return batch_collect(b, statuses, stats);
 }
 
@@ -950,11 +1085,11 @@ qg_status qg_batch_capture(qg_batch_t b, int method, int order, int scheme, doub
   }
   // function attributes are set here, outside the capture, by a zero-instance
   // launch that the kernel leaves immediately
-  QG_TRY(batch_launch(b, P, 0, b->cluster, b->ctas_per_sm, b->nb_pref));
+  QG_TRY(batch_launch(b, P, false));
   QG_TRY(cudaStreamSynchronize(b->stream));
   cudaGraph_t g = nullptr;
   QG_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = batch_launch(b, P, b->n, b->cluster, b->ctas_per_sm, b->nb_pref);
+  cudaError_t e = batch_launch(b, P, true);
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
@@ -968,69 +1103,78 @@ qg_status qg_batch_capture(qg_batch_t b, int method, int order, int scheme, doub
 }
 
 qg_status qg_batch_autotune(qg_batch_t b, int method, int order, int scheme, double dt, int64_t trial_steps,
-                            const qg_solver_opts* opts, double* ms_out /* 4 entries or NULL */) {
+                            const qg_solver_opts* opts, double* ms_out /* 6 entries or NULL */) {
   if (!b || trial_steps < 1) return QG_ERR_INVALID_ARG;
   StepPlan P;
   qg_status st = build_plan(method, order, scheme, dt, trial_steps, opts, &P);
   if (st != QG_OK) return st;
-  // save every state, time each candidate launch shape on the real batch,
-  // restore the states after each trial
+  // save every state, time each candidate launch shape of each grid-size
+  // class on the class's own instances, restore the states after each trial
   std::vector<InstDesc> descs(b->n);
   QG_TRY(cudaMemcpy(descs.data(), b->d_desc, sizeof(InstDesc) * b->n, cudaMemcpyDeviceToHost));
   size_t total = 0;
   for (const InstDesc& d : descs) total += (size_t)d.S * d.n;
   double2* save = nullptr;
   QG_TRY(cudaMalloc(&save, sizeof(double2) * total));
-  auto copy_all = [&](bool to_save) -> cudaError_t {
+  auto copy_class = [&](int c, bool to_save) -> cudaError_t {
     size_t off = 0;
-    for (const InstDesc& d : descs) {
+    for (int k = 0; k < b->n; ++k) {
+      const InstDesc& d = descs[k];
       const size_t len = (size_t)d.S * d.n;
-      cudaError_t e = to_save ? cudaMemcpyAsync(save + off, d.psi, sizeof(double2) * len, cudaMemcpyDeviceToDevice,
-                                                b->stream)
-                              : cudaMemcpyAsync(d.psi, save + off, sizeof(double2) * len, cudaMemcpyDeviceToDevice,
-                                                b->stream);
-      if (e != cudaSuccess) return e;
+      if (c < 0 || (k >= b->cls_start[c] && k < b->cls_start[c] + b->cls_count[c])) {
+        cudaError_t e = to_save ? cudaMemcpyAsync(save + off, d.psi, sizeof(double2) * len,
+                                                  cudaMemcpyDeviceToDevice, b->stream)
+                                : cudaMemcpyAsync(d.psi, save + off, sizeof(double2) * len,
+                                                  cudaMemcpyDeviceToDevice, b->stream);
+        if (e != cudaSuccess) return e;
+      }
       off += len;
     }
     return cudaSuccess;
   };
-  // {CTAs per SM, surfaces per FFT batch, cluster size}: the one-CTA form in
-  // four shapes, then the shared-memory cluster form at the smallest cluster
-  // that holds the largest instance and at twice that size
-  int g0 = 0;
-  for (int G = 1; G <= 16 && !g0; G *= 2)
-    if (batch_cluster_smem(b, G, P.restart) > 0) g0 = G;
-  const int cand[6][3] = {{1, 0, 0}, {1, 1, 0}, {2, 0, 0}, {2, 1, 0}, {1, 0, g0}, {1, 0, g0 > 0 && g0 < 16 ? 2 * g0 : 0}};
-  double best = 1e300;
-  int bi = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  if (e == cudaSuccess) e = copy_all(true);
-  for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
-    float ms = -1.f;
-    if (c >= 4 && (cand[c][2] == 0 || batch_cluster_smem(b, cand[c][2], P.restart) == 0)) {
-      if (ms_out) ms_out[c] = -1.0;
-      continue;
+  if (e == cudaSuccess) e = copy_class(-1, true);
+  for (int c = 0; c < b->nclass && e == cudaSuccess; ++c) {
+    // {CTAs per SM, surfaces per FFT batch, cluster size}: the one-CTA form
+    // in four shapes, then the cluster form at the smallest cluster size that
+    // holds the class and at twice that size
+    int g0 = 0;
+    for (int G = 1; G <= 16 && !g0; G *= 2)
+      if (class_cluster_smem(b, c, G, P.restart) > 0) g0 = G;
+    const int cand[6][3] = {{1, 0, 0}, {1, 1, 0}, {2, 0, 0}, {2, 1, 0}, {1, 0, g0},
+                            {1, 0, g0 > 0 && g0 < 16 ? 2 * g0 : 0}};
+    double best = 1e300;
+    int bi = 0;
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+      float ms = -1.f;
+      if (k >= 4 && (cand[k][2] == 0 || class_cluster_smem(b, c, cand[k][2], P.restart) == 0)) {
+        if (ms_out && c == 0) ms_out[k] = -1.0;
+        continue;
+      }
+      e = cudaEventRecord(e0, b->stream);
+      cudaError_t el = class_launch(b, c, P, true, cand[k][0], cand[k][1], cand[k][2]);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (el == cudaSuccess && e == cudaSuccess) {
+        cudaEventElapsedTime(&ms, e0, e1);
+      } else if (el == cudaErrorInvalidConfiguration) {
+        cudaGetLastError();   // shape does not fit: skip it
+        ms = -1.f;
+      } else if (e == cudaSuccess) {
+        e = el;
+      }
+      if (ms_out && c == 0) ms_out[k] = ms;
+      if (ms > 0.f && ms < best) {
+        best = ms;
+        bi = k;
+      }
+      if (e == cudaSuccess) e = copy_class(c, false);
     }
-    e = cudaEventRecord(e0, b->stream);
-    cudaError_t el = batch_launch(b, P, b->n, cand[c][2], cand[c][0], cand[c][1]);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    if (el == cudaSuccess && e == cudaSuccess) {
-      cudaEventElapsedTime(&ms, e0, e1);
-    } else if (el == cudaErrorInvalidConfiguration) {
-      cudaGetLastError();   // shape does not fit: skip it
-      ms = -1.f;
-    } else if (e == cudaSuccess) {
-      e = el;
-    }
-    if (ms_out) ms_out[c] = ms;
-    if (ms > 0.f && ms < best) {
-      best = ms;
-      bi = c;
-    }
-    if (e == cudaSuccess) e = copy_all(false);
+    b->cls_ctas[c] = cand[bi][0];
+    b->cls_nb[c] = cand[bi][1];
+    b->cls_cluster[c] = cand[bi][2];
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e0) cudaEventDestroy(e0);
@@ -1040,10 +1184,7 @@ qg_status qg_batch_autotune(qg_batch_t b, int method, int order, int scheme, dou
     set_err("qg_batch_autotune", e);
     return QG_ERR_CUDA;
   }
-  b->ctas_per_sm = cand[bi][0];
-  b->nb_pref = cand[bi][1];
-  b->cluster = cand[bi][2];
-  if (b->graph) {   // a captured graph used the old launch shape
+  if (b->graph) {   // a captured graph used the old launch shapes
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
@@ -1052,16 +1193,31 @@ qg_status qg_batch_autotune(qg_batch_t b, int method, int order, int scheme, dou
 
 qg_status qg_batch_tuning(qg_batch_t b, int* ctas_per_sm, int* surfaces_per_fft) {
   if (!b) return QG_ERR_INVALID_ARG;
-  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
-  if (surfaces_per_fft) *surfaces_per_fft = b->nb_pref;
+  if (ctas_per_sm) *ctas_per_sm = b->cls_ctas[0];
+  if (surfaces_per_fft) *surfaces_per_fft = b->cls_nb[0];
+  return QG_OK;
+}
+
+qg_status qg_batch_classes(qg_batch_t b, int* nclass, int* grid_n, int* count, int* ctas_per_sm,
+                           int* surfaces_per_fft, int* cluster) {
+  if (!b || !nclass) return QG_ERR_INVALID_ARG;
+  *nclass = b->nclass;
+  for (int c = 0; c < b->nclass; ++c) {
+    if (grid_n) grid_n[c] = b->cls_n[c];
+    if (count) count[c] = b->cls_count[c];
+    if (ctas_per_sm) ctas_per_sm[c] = b->cls_ctas[c];
+    if (surfaces_per_fft) surfaces_per_fft[c] = b->cls_nb[c];
+    if (cluster) cluster[c] = b->cls_cluster[c];
+  }
   return QG_OK;
 }
 
 qg_status qg_batch_set_cluster(qg_batch_t b, int G) {
   if (!b || G < 0) return QG_ERR_INVALID_ARG;
-  if (G > 0 && batch_cluster_smem(b, G, QG_MAX_RESTART) == 0 && batch_cluster_smem(b, G, 4) == 0)
-    return QG_ERR_UNSUPPORTED;
-  b->cluster = G;
+  for (int c = 0; c < b->nclass && G > 0; ++c)
+    if (class_cluster_smem(b, c, G, QG_MAX_RESTART) == 0 && class_cluster_smem(b, c, G, 4) == 0)
+      return QG_ERR_UNSUPPORTED;
+  for (int c = 0; c < b->nclass; ++c) b->cls_cluster[c] = G;
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -1071,7 +1227,7 @@ qg_status qg_batch_set_cluster(qg_batch_t b, int G) {
 
 qg_status qg_batch_cluster(qg_batch_t b, int* G) {
   if (!b || !G) return QG_ERR_INVALID_ARG;
-  *G = b->cluster;
+  *G = b->cls_cluster[0];
   return QG_OK;
 }
 

@@ -216,6 +216,8 @@ struct HOp {
   const R* V;
   const R* F;
   C* U;          // scratch vector (S * n)
+  int diab;      // 1: the diabatic representation, H = -hbar^2/2m D^2 + W, with
+                 // V = diag W and F = the upper triangle of W (symmetric)
 };
 
 // Number of leading radix-8 passes of a plan.
@@ -277,11 +279,13 @@ __device__ __forceinline__ void fft_pass(C* gbuf, int n, int nb, int L, const C*
 }
 
 // Last forward pass (block length RD, no twiddles), multiplication by i k / n
-// at the digit-reversed positions, first inverse pass -- all in registers.
+// (or, second = 1, by (i k)^2 / n = -n (k/n)^2) at the digit-reversed
+// positions, first inverse pass -- all in registers.
 template <int RD, typename C, typename R>
-__device__ __forceinline__ void fft_center(C* gbuf, int n, int nb, const R* __restrict__ kd) {
+__device__ __forceinline__ void fft_center(C* gbuf, int n, int nb, const R* __restrict__ kd, int second = 0) {
   C* buf = in_dyn_smem(gbuf);
   const int total = (nb * n) / RD;
+  const R mn = -(R)n;
   for (int b = threadIdx.x; b < total; b += kThreads) {
     const int e0 = b * RD;
     const int pos = e0 & (n - 1);
@@ -289,10 +293,18 @@ __device__ __forceinline__ void fft_center(C* gbuf, int n, int nb, const R* __re
 #pragma unroll
     for (int r = 0; r < RD; ++r) x[r] = buf[spad<C>(e0 + r)];
     dft<RD, false>(x);
+    if (second) {
 #pragma unroll
-    for (int r = 0; r < RD; ++r) {
-      const R k = kd[pos + r];
-      x[r] = cmk<C>(-k * x[r].y, k * x[r].x);
+      for (int r = 0; r < RD; ++r) {
+        const R k = kd[pos + r];
+        x[r] = cscale(mn * k * k, x[r]);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < RD; ++r) {
+        const R k = kd[pos + r];
+        x[r] = cmk<C>(-k * x[r].y, k * x[r].x);
+      }
     }
     dft<RD, true>(x);
 #pragma unroll
@@ -306,9 +318,10 @@ __device__ __forceinline__ void fft_center(C* gbuf, int n, int nb, const R* __re
 // instruction-cache misses than an inlined copy at every site).
 // src (optional): take the input from src (nb unpadded vectors) instead of
 // buf; the first forward pass reads it.
+// second = 1: the second derivative D^2 instead (same transforms).
 template <typename R>
 __device__ __noinline__ void spectral_derivative(typename Cx<R>::T* buf, int nb, const HOp<R>& H,
-                                                 const typename Cx<R>::T* src = nullptr) {
+                                                 const typename Cx<R>::T* src = nullptr, int second = 0) {
   using C = typename Cx<R>::T;
   const int n = H.n, np = H.npass, n8 = H.n8;
   const C* tw = H.tw;
@@ -332,9 +345,9 @@ __device__ __noinline__ void spectral_derivative(typename Cx<R>::T* buf, int nb,
     __syncthreads();
   }
   if (np - 1 < n8)
-    fft_center<8>(buf, n, nb, kd);
+    fft_center<8>(buf, n, nb, kd, second);
   else
-    fft_center<4>(buf, n, nb, kd);
+    fft_center<4>(buf, n, nb, kd, second);
   __syncthreads();
   for (int i = np - 2; i >= 0; --i) {
     const int RD = i < n8 ? 8 : 4;
@@ -360,6 +373,75 @@ __device__ __forceinline__ R coupling(const R* __restrict__ F, int n, int S, int
   }
 }
 
+// Diabatic coupling W_st (s != t) from the stored upper triangle (symmetric).
+template <typename R>
+__device__ __forceinline__ R wcoupling(const R* __restrict__ F, int n, int S, int s, int t, int j) {
+  const int a = s < t ? s : t, b = s < t ? t : s;
+  const int p = a * S - (a * (a + 1)) / 2 + (b - a - 1);
+  return __ldg(F + (size_t)p * n + j);
+}
+
+// y = e z + a x + c (H x) in the diabatic representation (Sec. II E):
+// H = -hbar^2/(2m) D^2 1 + W(q), two transforms per surface and the
+// pointwise symmetric W.  DOTS: also Re<x, y> and ||y||^2 (raw sums) in
+// dots[0..1].  y may alias x or z.
+template <typename R, bool DOTS>
+__device__ __forceinline__ void apply_h_diabatic(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
+                                                 const typename Cx<R>::T* x, typename Cx<R>::T* y,
+                                                 const typename Cx<R>::T* z, R e, R a, typename Cx<R>::T c, R* red,
+                                                 R* dots) {
+  using C = typename Cx<R>::T;
+  const int n = H.n, S = H.S;
+  const int ln = ilog2(n);
+  const R* F = H.F;
+  const R* V = H.V;
+  const R mh = -H.h2m;
+  const int nb = (S <= nb_cap) ? S : 1;
+  C* sb = in_dyn_smem(sbuf);
+  R d[2] = {(R)0, (R)0};
+  // the coupling reads x at other surfaces' points, so results go straight
+  // to y only when all surfaces form one batch and y does not alias x; else
+  // H x is formed in U first and combined in a last pass
+  const bool whole = nb == S && (const void*)y != (const void*)x;
+  for (int s0 = 0; s0 < S; s0 += nb) {
+    spectral_derivative<R>(sbuf, nb, H, x + (size_t)s0 * n, 1);
+    for (int i = threadIdx.x; i < nb * n; i += kThreads) {
+      const int s = s0 + (i >> ln), j = i & (n - 1);
+      const C xs = x[s * n + j];
+      const R v = __ldg(V + s * n + j);
+      C acc = cmk<C>(fma(mh, sb[spad<C>(i)].x, v * xs.x), fma(mh, sb[spad<C>(i)].y, v * xs.y));
+      for (int t = 0; t < S; ++t)
+        if (t != s) acc = caxpy_r(wcoupling(F, n, S, s, t, j), x[t * n + j], acc);
+      if (whole) {
+        C out = caxpy(c, acc, cmk<C>(a * xs.x, a * xs.y));
+        if (e != (R)0) out = caxpy_r(e, z[s * n + j], out);
+        y[s * n + j] = out;
+        if (DOTS) {
+          d[0] = fma(xs.x, out.x, fma(xs.y, out.y, d[0]));
+          d[1] = fma(out.x, out.x, fma(out.y, out.y, d[1]));
+        }
+      } else {
+        H.U[s * n + j] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  if (!whole) {
+    for (int i = threadIdx.x; i < S * n; i += kThreads) {
+      const C xs = x[i];
+      C out = caxpy(c, H.U[i], cmk<C>(a * xs.x, a * xs.y));
+      if (e != (R)0) out = caxpy_r(e, z[i], out);
+      y[i] = out;
+      if (DOTS) {
+        d[0] = fma(xs.x, out.x, fma(xs.y, out.y, d[0]));
+        d[1] = fma(out.x, out.x, fma(out.y, out.y, d[1]));
+      }
+    }
+    __syncthreads();
+  }
+  if (DOTS) cta_sum<2>(d, red, dots);
+}
+
 // y = e z + a x + c (H x), H of Eq. (adiab_mol_ham) by the dynamic Fourier
 // method.  With A = p - i hbar F = -i hbar (D + F), the Hamiltonian equals
 // -hbar^2/(2m) (D + F)^2 + V exactly (F real antisymmetric, D the spectral
@@ -373,6 +455,10 @@ __device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T
                                               const typename Cx<R>::T* x, typename Cx<R>::T* y,
                                               const typename Cx<R>::T* z, R e, R a, typename Cx<R>::T c) {
   using C = typename Cx<R>::T;
+  if (H.diab) {
+    apply_h_diabatic<R, false>(H, sbuf, nb_cap, x, y, z, e, a, c, nullptr, nullptr);
+    return;
+  }
   const int n = H.n, S = H.S;
   const int ln = ilog2(n);
   C* U = H.U;
@@ -428,6 +514,10 @@ __device__ __forceinline__ void apply_h_staged(const HOp<R>& H, typename Cx<R>::
                                                typename Cx<R>::T* y, const typename Cx<R>::T* z, R e, R a,
                                                typename Cx<R>::T c, R* red, R* dots) {
   using C = typename Cx<R>::T;
+  if (H.diab) {
+    apply_h_diabatic<R, DOTS>(H, sbuf, nb_cap, x, y, z, e, a, c, red, dots);
+    return;
+  }
   const int n = H.n, S = H.S;
   const int ln = ilog2(n);
   const R* F = H.F;

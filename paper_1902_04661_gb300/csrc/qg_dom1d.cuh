@@ -65,6 +65,7 @@ __device__ __forceinline__ HOp<double> hop64(const InstDesc& I, double2* U) {
   H.V = I.V;
   H.F = I.F;
   H.U = U;
+  H.diab = I.rep;
   return H;
 }
 
@@ -80,6 +81,7 @@ __device__ __forceinline__ HOp<float> hop32(const InstDesc& I, float2* U) {
   H.V = I.V32;
   H.F = I.F32;
   H.U = U;
+  H.diab = I.rep;
   return H;
 }
 

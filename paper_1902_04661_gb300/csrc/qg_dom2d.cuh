@@ -345,6 +345,8 @@ static __device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_
   D.gm = dyn + fft_bytes + stage_bytes;
   D.red = red;
   for (int d = 0; d < 2; ++d) {
+    D.H64[d].diab = 0;
+    D.H32[d].diab = 0;
     D.H64[d].n = I.n[d];
     D.H64[d].S = I.S;
     D.H64[d].npass = I.npass[d];

@@ -12,6 +12,7 @@
 #define QG_MAX_RESTART 64
 #define QG_MAX_PASSES 8
 #define QG_MAX_FRACTIONS 128
+#define QG_MAX_CLASSES 12
 #define QG_MIN_N 8
 #define QG_MAX_N 8192
 #define QG_THREADS 256
@@ -50,6 +51,9 @@ struct qg_model {
   double* d_F;  // D * S(S-1)/2 * ntot (upper triangle)
   float* d_V32;  // FP32 copies for the mixed-precision inner solves
   float* d_F32;
+  int rep;       // 0: adiabatic (V, F); 1: diabatic representation (V = diag W, F = upper triangle of W)
+  double* d_O;   // adiabatic models built from W: O(q) per point, O[(j S + r) S + i] = component r of
+                 // adiabatic state i (ascending), or null
 };
 
 struct InstDesc;
@@ -110,6 +114,7 @@ struct InstDesc {
   double2* grad;       // in: dL/dpsi(t_f); out: dL/dpsi(0)   (S * n)
   double* gV;          // += dL/dV   (S * n)
   double* gF;          // += dL/dF   (S(S-1)/2 * n)
+  int rep;             // 1: diabatic representation (see qg_model)
 };
 
 // One instance on a 2-D grid (all CTAs of a cooperative launch share it).
@@ -173,12 +178,15 @@ struct qg_batch {
   qg_step_stats* h_stats;   // pinned, per table entry
   cudaGraphExec_t graph;    // captured run, or null
   bool adjoint_ready;       // every state has checkpoint and gradient buffers
-  int ctas_per_sm;          // launch shape chosen by qg_batch_autotune (default 1)
-  int nb_pref;              // surfaces per FFT batch (0 = as many as fit)
-  int cluster;              // > 0: the shared-memory cluster form with this many CTAs per instance
-  int all_fp64;             // every state is QG_C128 (the cluster form needs it)
-  int min_n, max_len;       // smallest grid and largest S * N of the batch
-  unsigned nmask[QG_MAX_S + 1];  // bit k of nmask[S]: an instance has S surfaces and 2^k points
+  int all_fp64;             // every state is adiabatic QG_C128 (the cluster form needs it)
+  // Grid-size classes: the table is ordered by N (then S) descending, and
+  // entries [cls_start[c], cls_start[c] + cls_count[c]) share N = cls_n[c]
+  // (cls_S[c] = their largest S).  Each class is one persistent launch with
+  // its own shape: CTAs per SM, surfaces per FFT batch, cluster size (> 0:
+  // the shared-memory cluster form); qg_batch_autotune picks them.
+  int nclass;
+  int cls_start[QG_MAX_CLASSES], cls_count[QG_MAX_CLASSES], cls_n[QG_MAX_CLASSES], cls_S[QG_MAX_CLASSES];
+  int cls_ctas[QG_MAX_CLASSES], cls_nb[QG_MAX_CLASSES], cls_cluster[QG_MAX_CLASSES];
 };
 
 // Launch wrappers (qg_kernels.cu).
@@ -250,4 +258,9 @@ cudaError_t qg_launch_to_f32(const double* d_in, float* d_out, size_t n, cudaStr
 cudaError_t qg_launch_fieldsS(const double* d_W, const double* d_dW, int n, int S, double* d_V, double* d_F,
                               double* d_vec, cudaStream_t st);
 cudaError_t qg_launch_fields2(const double* d_W, const double* d_dW, int n, int D, double* d_V, double* d_F,
-                              cudaStream_t st);
+                              double* d_O, cudaStream_t st);
+cudaError_t qg_launch_diabatic_fields(const double* d_W, int n, int S, double* d_V, double* d_F, cudaStream_t st);
+cudaError_t qg_launch_rotate(const double* d_O, const double2* in, double2* out, int n, int S, int to_adiabatic,
+                             cudaStream_t st);
+cudaError_t qg_launch_interpolate(const double2* src, int ns, double qmin_s, double len_s, double2* coef,
+                                  double2* dst, int nd, double qmin_d, double dq_d, int S, cudaStream_t st);

@@ -103,8 +103,12 @@ __global__ void __launch_bounds__(QG_THREADS)
 // expression (W12' Delta - W12 Delta') / (W12^2 + Delta^2) is evaluated in the
 // algebraically identical form (dW W12' - W12 dW') / (dW^2 + 4 W12^2),
 // dW = W22 - W11, which has no cancellation where W12 is small.
+// O(q) of Eq. (..._orthogonal_transformation) with columns in ascending
+// order: ground = (-Delta, W12) / norm (the paper's state 2), excited =
+// (W12, Delta) / norm (state 1), Delta = V_1 - W11 = dW/2 + r taken as
+// W12^2 / (r - dW/2) when dW < 0 (no cancellation); O is written when given.
 __global__ void fields2_kernel(const double* __restrict__ W, const double* __restrict__ dW, int n, int D, double* V,
-                               double* F) {
+                               double* F, double* O) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const double w11 = W[j], w12 = W[n + j], w22 = W[2 * n + j];
@@ -113,6 +117,22 @@ __global__ void fields2_kernel(const double* __restrict__ W, const double* __res
   const double r = hypot(0.5 * dw, w12);
   V[j] = wbar - r;
   V[n + j] = wbar + r;
+  if (O) {
+    const double del = dw >= 0.0 ? 0.5 * dw + r : (r - 0.5 * dw > 0.0 ? w12 * w12 / (r - 0.5 * dw) : 0.0);
+    const double nrm = hypot(del, w12);
+    double* o = O + (size_t)j * 4;   // o[r * 2 + i]: component r of state i
+    if (nrm > 0.0) {
+      o[0] = -del / nrm;
+      o[2] = w12 / nrm;
+      o[1] = w12 / nrm;
+      o[3] = del / nrm;
+    } else {   // uncoupled with W22 < W11: the ground state is diabatic state 1
+      o[0] = 0.0;
+      o[2] = 1.0;
+      o[1] = 1.0;
+      o[3] = 0.0;
+    }
+  }
   for (int d = 0; d < D; ++d) {
     const double* g = dW + (size_t)d * 3 * n;
     const double d11 = g[j], d12 = g[n + j], d22 = g[2 * n + j];
@@ -233,6 +253,87 @@ __global__ void fieldsS_gauge_kernel(int n, int S, double* F, double* vec) {
   }
 }
 
+// Diabatic representation: V = the diagonal of W, F = its upper triangle
+// (pairs s < t in lexicographic order, as for the adiabatic couplings).
+__global__ void diabatic_fields_kernel(const double* __restrict__ W, int n, int S, double* V, double* F) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int t = 0, p = 0;
+  for (int a = 0; a < S; ++a)
+    for (int b = a; b < S; ++b) {
+      const double w = W[(size_t)t * n + j];
+      if (a == b)
+        V[(size_t)a * n + j] = w;
+      else
+        F[(size_t)(p++) * n + j] = w;
+      ++t;
+    }
+}
+
+// out = O^T in (to_adiabatic, Eq. psi_diab2adiab) or O in at every point.
+__global__ void rotate_kernel(const double* __restrict__ O, const double2* __restrict__ in, double2* out, int n, int S,
+                              int to_adiabatic) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double* o = O + (size_t)j * S * S;
+  double2 v[QG_MAX_S];
+  for (int r = 0; r < S; ++r) v[r] = in[(size_t)r * n + j];
+  for (int i = 0; i < S; ++i) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int r = 0; r < S; ++r) {
+      const double c = to_adiabatic ? o[r * S + i] : o[i * S + r];
+      acc = caxpy_r(c, v[r], acc);
+    }
+    out[(size_t)i * n + j] = acc;
+  }
+}
+
+// Trigonometric interpolation (Appendix B), step 1: the DFT coefficients
+// c_k = sum_j v_j exp(-2 pi i j k / n) of every surface by direct sums (the
+// phase from the exact integer j k mod n).
+__global__ void interp_coef_kernel(const double2* __restrict__ src, int n, int S, double2* coef) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= S * n) return;
+  const int s = idx / n, k = idx - s * n;
+  const double2* v = src + (size_t)s * n;
+  double2 acc = make_double2(0.0, 0.0);
+  long long ph = 0;
+  for (int j = 0; j < n; ++j) {
+    double sn, cs;
+    sincospi(-2.0 * (double)ph / (double)n, &sn, &cs);
+    acc = caxpy(make_double2(cs, sn), v[j], acc);
+    ph += k;
+    if (ph >= n) ph -= n;
+  }
+  coef[idx] = acc;
+}
+
+// Step 2: p(q) = (1/n) sum_k c_k exp(i k' 2 pi (q - qmin) / L), k' the signed
+// frequency, the Nyquist coefficient taken as a cosine (split between +-n/2).
+__global__ void interp_eval_kernel(const double2* __restrict__ coef, int ns, double qmin_s, double len_s,
+                                   double2* dst, int nd, double qmin_d, double dq_d, int S) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= S * nd) return;
+  const int s = idx / nd, i = idx - s * nd;
+  const double x = (qmin_d + dq_d * i - qmin_s) / len_s;
+  const double2* c = coef + (size_t)s * ns;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k = 0; k < ns; ++k) {
+    const int m = k < ns / 2 ? k : k - ns;
+    double t = (double)m * x;
+    t -= rint(t);
+    double sn, cs;
+    if (k == ns / 2) {
+      cs = cospi(2.0 * t);
+      sn = 0.0;
+    } else {
+      sincospi(2.0 * t, &sn, &cs);
+    }
+    acc = caxpy(make_double2(cs, sn), c[k], acc);
+  }
+  dst[idx] = cscale(1.0 / ns, acc);
+}
+
 __global__ void to_f32_kernel(const double* __restrict__ in, float* out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
@@ -330,8 +431,28 @@ cudaError_t qg_launch_fieldsS(const double* d_W, const double* d_dW, int n, int 
 }
 
 cudaError_t qg_launch_fields2(const double* d_W, const double* d_dW, int n, int D, double* d_V, double* d_F,
-                              cudaStream_t st) {
-  qg::fields2_kernel<<<(n + 255) / 256, 256, 0, st>>>(d_W, d_dW, n, D, d_V, d_F);
+                              double* d_O, cudaStream_t st) {
+  qg::fields2_kernel<<<(n + 255) / 256, 256, 0, st>>>(d_W, d_dW, n, D, d_V, d_F, d_O);
+  return cudaGetLastError();
+}
+
+cudaError_t qg_launch_diabatic_fields(const double* d_W, int n, int S, double* d_V, double* d_F, cudaStream_t st) {
+  qg::diabatic_fields_kernel<<<(n + 255) / 256, 256, 0, st>>>(d_W, n, S, d_V, d_F);
+  return cudaGetLastError();
+}
+
+cudaError_t qg_launch_rotate(const double* d_O, const double2* in, double2* out, int n, int S, int to_adiabatic,
+                             cudaStream_t st) {
+  qg::rotate_kernel<<<(n + 255) / 256, 256, 0, st>>>(d_O, in, out, n, S, to_adiabatic);
+  return cudaGetLastError();
+}
+
+cudaError_t qg_launch_interpolate(const double2* src, int ns, double qmin_s, double len_s, double2* coef,
+                                  double2* dst, int nd, double qmin_d, double dq_d, int S, cudaStream_t st) {
+  qg::interp_coef_kernel<<<(S * ns + 127) / 128, 128, 0, st>>>(src, ns, S, coef);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  qg::interp_eval_kernel<<<(S * nd + 127) / 128, 128, 0, st>>>(coef, ns, qmin_s, len_s, dst, nd, qmin_d, dq_d, S);
   return cudaGetLastError();
 }
 

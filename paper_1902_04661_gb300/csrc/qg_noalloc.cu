@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(QG_THREADS, 1)
   I.grad = nullptr;
   I.gV = nullptr;
   I.gF = nullptr;
+  I.rep = 0;
   qg_step_stats* st = reinterpret_cast<qg_step_stats*>(base + kNaWorkBytes + kNaTwBytes + kNaKdBytes);
   const Smem sm = carve_smem(dyn, in.n, nb_cap, P.restart);
   run_instance(I, P, sm, st, red, sc);

@@ -102,3 +102,27 @@ def test_full_size_2d_mixed_vs_fp64(qglib, cuda):
     got = st.apply_h()
     want = (k1 ** 2 / 6.0 + k2 ** 2 / 10.0) * pw
     assert np.abs(got[0] - want).max() < 1e-11 * np.abs(want).max()
+
+
+def test_full_size_2d_hpsi_and_implicit_equation_vs_matrix_free_oracle(qglib, cuda):
+    # 256 x 256: H psi element by element against the oracle's 2-D
+    # matrix-free H, and one midpoint step of each precision form through its
+    # implicit equation (1 + i tau H) chi = psi0, chi = (psi0 + psi1)/2
+    ns = (256, 256)
+    p = wl.MODEL2D_PARAMS
+    g, m, W, dW, (q1, q2) = _model2d(qglib, ns)
+    V, F = ofields.two_state(W, dW)
+    q0, p0, s0 = wl.model2d_initial()
+    psi0 = oinit.state_on_surface(2, 1, oinit.gaussian([q1, q2], q0, [2.0, -1.0], s0))
+    h = lambda x: oham.apply_h_matrix_free_2d(list(p["qmin"]), list(p["qmax"]), ns, list(p["mass"]), V, F, x)
+    st = qglib.State(m)
+    st.set(psi0)
+    assert rel_l2(st.apply_h(), h(psi0)) < 1e-12
+    dt = 0.5 * FS
+    for prec in (qglib.QG_C128, qglib.QG_C64_MIXED):
+        s = qglib.State(m, precision=prec)
+        s.set(psi0)
+        s.propagate(qglib.QG_MIDPOINT, 2, qglib.QG_SUZUKI, dt, 1, qglib.default_solver_opts(tol=1e-14))
+        chi = 0.5 * (psi0 + s.get())
+        r = chi + 0.5j * dt * h(chi) - psi0
+        assert np.linalg.norm(r) / np.linalg.norm(psi0) < 1e-12

@@ -1,5 +1,6 @@
 """Pins of the oracle's dense adiabatic Hamiltonian, Eq. (adiab_mol_ham)."""
 import numpy as np
+import pytest
 
 import workloads as wl
 from oracle import fields, grid, hamiltonian as ham
@@ -102,3 +103,16 @@ def test_two_dimensional_adiabatic_hamiltonian_has_the_diabatic_spectrum():
     Hd[:N, N:] += np.diag(W[1].reshape(-1))
     Hd[N:, :N] += np.diag(W[1].reshape(-1))
     np.testing.assert_allclose(np.linalg.eigvalsh(Ha)[:10], np.linalg.eigvalsh(Hd)[:10], rtol=0, atol=5e-8)
+
+
+@pytest.mark.parametrize("ns,S", [((8, 8), 2), ((12, 16), 3)])
+def test_matrix_free_2d_equals_dense(ns, S):
+    # the 2-D matrix-free H psi is the dense H of Eq. (adiab_mol_ham) applied
+    import workloads as wl
+    qmin, qmax, mass = [-3.0, -2.0], [3.0, 2.5], [7.0, 11.0]
+    V, F = wl.random_adiabatic_fields(S, 2, ns, seed=60 + S)
+    psi = wl.random_psi(S, ns, seed=61 + S)
+    H = ham.dense_h(qmin, qmax, list(ns), mass, V, F)
+    want = ham.apply_h(H, psi)
+    got = ham.apply_h_matrix_free_2d(qmin, qmax, ns, mass, V, F, psi)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-13
