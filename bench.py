@@ -130,24 +130,41 @@ def _peaks():
 
 def fp64_peak_tflops(sm_mhz=None):
     """FP64 FMA peak: 152 SMs x 2 DFMA/clock (4 flops) x SM clock.  The rate
-    of 2 DFMA per SM per clock was measured on GB300 with an FMA-chain probe
-    (1.20 TFLOP/s at 2002 MHz)."""
+    of 2 DFMA per SM per clock is measured on the GB300 itself by the
+    library's probe (qg_probe_fp64), reported beside every roofline."""
     mhz = sm_mhz or 2070.0
     return 152 * 4 * mhz * 1e6 / 1e12
 
 
-# DRAM bytes (read + write) of one propagate_kernel launch of the default
-# workload (FP64, Lanczos, Euler start, one wavepacket per SM), from one ncu
-# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum).
-# Reported only for that configuration; it must be re-measured whenever the
-# kernel changes.
-NCU_TRAFFIC_BYTES = 5.079719e9 + 18.604768e9
+# DRAM traffic of one propagate_kernel launch of the default workload comes
+# from the kept ncu record (profiles/propagate_kernel_nai_n2048_traffic.json),
+# which names the hash of the kernel's sources it was captured with; when the
+# sources have changed since, the bench reports no traffic.
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "propagate_kernel_nai_n2048_traffic.json")
+KERNEL_SOURCES = ["qg_propagate.cu", "qg_dom1d.cuh", "qg_solver.cuh", "qg_device.cuh", "qg_internal.h"]
 
 
-def _traffic(args, B):
+def kernel_sources_sha16():
+    """Hash of the one-CTA propagator's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1902_04661_gb300", "csrc")
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(args, B, tuning=None):
     default = (args.precision == "fp64" and args.solver == "lanczos" and _guess(args) == 0 and B == 152
                and getattr(args, "workload", "nai") == "nai")
-    return NCU_TRAFFIC_BYTES if default else None
+    if not default or not os.path.exists(TRAFFIC_RECORD):
+        return None
+    rec = json.load(open(TRAFFIC_RECORD))
+    if rec.get("sources_sha16") != kernel_sources_sha16():
+        return None
+    if tuning is not None and rec.get("surfaces_per_fft") not in (None, tuning.get("surfaces_per_fft")):
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def _guess(args):
@@ -254,6 +271,7 @@ def run_ours(args):
     clocks = clk.summary()
     peak = fp64_peak_tflops()
     achieved = flops / avg_launch_s / 1e12
+    probe = qg.probe_fp64()
 
     # end to end through the C-ABI: pinned host -> device, step, device -> host
     len_state = S * N
@@ -303,9 +321,11 @@ def run_ours(args):
             "c64_hpsi_per_substep": sum(s["n_hpsi32"] for s in flat) / max(1, n_sub),
             "hbm_frac_if_streamed": abytes / avg_launch_s / 1e9 / mp.get("hbm_gbs", 6695.2),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": _traffic(args, B),
+                         "frac": achieved / peak, "traffic": _traffic(args, B, tuning),
                          "kernel": "qg::propagate_kernel",
-                         "peak_source": "FP64 FMA peak 152 SMs x 4 flop/clk x 2070 MHz (measured 2 DFMA/SM/clk)"},
+                         "peak_source": "FP64 FMA peak 152 SMs x 2 DFMA/clk (4 flop) x 2070 MHz",
+                         "probe": dict(probe, how="qg_probe_fp64: register FMA / add chains, 8 CTAs per SM, "
+                                                   "SM clock from clock64 against the global timer")},
             "gpu_launches": args.steps,
             "autotune": tuning,
             "clocks": clocks,
@@ -540,17 +560,26 @@ def run_batched(args):
     # every replay ran the same step; the statistics of the last one stand for each
     hpsi_pts = sum(s["n_hpsi"] * n * S for s, (n, S) in zip(st_, sizes))
     value = nmod * args.steps / (t_ms / 1e3)
-    # per-instance path: one qg_propagate launch per model, on a sample
-    ns = min(nmod, args.per_instance_sample)
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
+    # per-instance path filling the GPU: one qg_propagate launch per model
+    # (one CTA each), issued from 128 host threads on 128 streams so that
+    # up to 128 launches run at once
+    import concurrent.futures as cf
+    nthreads = 128
+    streams = [torch.cuda.Stream() for _ in range(nthreads)]
+    for i, st in enumerate(states):
+        st.set_stream(streams[i % nthreads])
+    ns = nmod if args.per_instance_sample <= 0 else min(nmod, args.per_instance_sample)
+
+    def lane(t):
+        for st in states[t:ns:nthreads]:
+            st.propagate(m_, o_, s_, dt, 1, opts)
+
     torch.cuda.synchronize()
-    t0.record(stream)
-    for st in states[:ns]:
-        st.propagate(m_, o_, s_, dt, 1, opts)
-    t1.record(stream)
+    w0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(nthreads) as ex:
+        list(ex.map(lane, range(nthreads)))
     torch.cuda.synchronize()
-    per_ms = t0.elapsed_time(t1)
+    per_ms = (time.perf_counter() - w0) * 1e3
     per_value = ns / (per_ms / 1e3)
     line = {"metric": METRIC, "value": value, "unit": "wavepacket-steps/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -562,6 +591,8 @@ def run_batched(args):
                        "launch": "one persistent launch per step, CUDA graph replay"},
             "hpsi_grid_point_applications_per_s": hpsi_pts * args.steps / (t_ms / 1e3),
             "per_instance_path": {"value": per_value, "unit": "wavepacket-steps/s", "sample_models": ns,
+                                  "launch": "one launch per model from 128 host threads on 128 streams "
+                                            "(wall clock)",
                                   "speedup_of_batched": value / per_value},
             "gpu_launches": args.steps, "clocks": clk.summary(), "autotune": tuning,
             "statuses_ok": sum(1 for x in stt if x == 0)}
@@ -620,6 +651,7 @@ def run_2d(args):
             st.propagate(1, 6, 1, dt, 1, opts)
         tune = st.autotune(1, 6, 1, dt, 1, opts) if not args.no_autotune else None
         st.set_gaussian(1, q0, p0, s0)
+        e_start = st.energy()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -627,7 +659,8 @@ def run_2d(args):
         s_ = st.propagate(1, 6, 1, dt, args.steps, opts)
         e1.record()
         torch.cuda.synchronize()
-        res[name] = dict(ms=e0.elapsed_time(e1), stats=s_, psi=st.get(), norm=st.norm(), tune=tune)
+        res[name] = dict(ms=e0.elapsed_time(e1), stats=s_, psi=st.get(), norm=st.norm(), tune=tune,
+                         energy_drift=abs(st.energy() - e_start) / max(1e-300, abs(e_start)))
     dv = np.prod([(p["qmax"][d] - p["qmin"][d]) / ns[d] for d in range(2)])
     err = float(np.linalg.norm(res["mixed"]["psi"] - res["fp64"]["psi"]) * np.sqrt(dv))
     err_ref = {k: float(np.linalg.norm(res[k]["psi"] - psi_ref) * np.sqrt(dv)) for k in ("mixed", "fp64")}
@@ -643,6 +676,8 @@ def run_2d(args):
                           "fp64_hpsi": res["fp64"]["stats"]["n_hpsi"]},
             "speedup_mixed_over_fp64": t_f / t_m,
             "mixed_vs_fp64_l2": err, "norm_drift": abs(res["mixed"]["norm"] - 1.0),
+            "drift": {k: {"norm": abs(res[k]["norm"] - 1.0), "energy_rel": res[k]["energy_drift"]}
+                      for k in ("mixed", "fp64")},
             # L2 error of each arm against FP64 at solver tol 1e-15, same steps
             "error_vs_tight_fp64": err_ref,
             "mixed_hpsi": {"fp64": res["mixed"]["stats"]["n_hpsi"], "c64": res["mixed"]["stats"]["n_hpsi32"]},
@@ -949,7 +984,7 @@ def main():
     ap.add_argument("--config2-n", default="2048,4096", help="grid sizes of the config2 error sweep")
     ap.add_argument("--models", type=int, default=0)
     ap.add_argument("--tol2d", type=float, default=1e-12, help="solver tolerance of the 2-D workload")
-    ap.add_argument("--per-instance-sample", type=int, default=64)
+    ap.add_argument("--per-instance-sample", type=int, default=0, help="models timed one launch each (0: all)")
     ap.add_argument("--tf", type=float, default=10500.0)
     ap.add_argument("--sweep-tol", type=float, default=1e-15)
     ap.add_argument("--sweep-dir", default="")

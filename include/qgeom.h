@@ -432,6 +432,16 @@ qg_status qg_propagate_noalloc(int N, double qmin, double qmax, int S, double ma
  * *passed = 0 when the time-out path works. */
 qg_status qg_selftest_barrier_timeout(int* timed_out, int* passed);
 
+/* FP64 throughput probe of the current device (not in the paper; the
+ * denominator of the FP64 roofline): chains of fused multiply-adds and of
+ * adds on registers over 8 CTAs per SM, timed with CUDA events, the SM clock
+ * read inside the kernel (clock64 against the global timer).  Writes the
+ * achieved rates in TFLOP/s (a fused multiply-add counts 2 flops, an add 1),
+ * the instructions per SM per clock of each, and the SM clock (GHz) during
+ * the FMA run; any pointer may be NULL.  Synchronous, about 0.2 s. */
+qg_status qg_probe_fp64(double* fma_tflops, double* add_tflops, double* fma_per_sm_clk, double* add_per_sm_clk,
+                        double* sm_ghz);
+
 /* Human-readable name of a status; message of the last CUDA error seen by
  * this thread. */
 const char* qg_status_string(qg_status st);

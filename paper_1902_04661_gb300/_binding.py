@@ -52,7 +52,7 @@ EXPORTED = [
     "qg_state_autotune", "qg_state_set_adjoint", "qg_propagate_ex", "qg_batch_run_ex", "qg_propagate_noalloc", "qg_status_string", "qg_last_error_string", "qg_version",
     "qg_state_set_cluster", "qg_cluster_size", "qg_batch_cluster", "qg_batch_set_cluster",
     "qg_create_model_diabatic_rep", "qg_diabatic_to_adiabatic", "qg_adiabatic_to_diabatic", "qg_interpolate",
-    "qg_batch_classes",
+    "qg_batch_classes", "qg_probe_fp64",
 ]
 
 
@@ -137,6 +137,7 @@ def lib():
             "qg_diabatic_to_adiabatic": (I, [P, P, P, I]),
             "qg_adiabatic_to_diabatic": (I, [P, P, P, I]),
             "qg_interpolate": (I, [P, P]),
+            "qg_probe_fp64": (I, [ctypes.POINTER(D)] * 5),
             "qg_batch_classes": (I, [P, ctypes.POINTER(I)] + [ctypes.POINTER(I)] * 5),
             "qg_cluster_size": (I, [I, I, I]),
             "qg_batch_cluster": (I, [P, ctypes.POINTER(ctypes.c_int)]),
@@ -503,6 +504,14 @@ def cluster_size(N, S, restart=30):
     """Smallest cluster size of the shared-memory cluster form that holds an
     instance of N points and S surfaces (0: none)."""
     return int(lib().qg_cluster_size(int(N), int(S), int(restart)))
+
+
+def probe_fp64():
+    """Measured FP64 rates of the current device: FMA and add TFLOP/s, the
+    instructions per SM per clock of each, and the SM clock (GHz) seen."""
+    v = [ctypes.c_double() for _ in range(5)]
+    _check(lib().qg_probe_fp64(*[ctypes.byref(x) for x in v]), "qg_probe_fp64")
+    return dict(zip(["fma_tflops", "add_tflops", "fma_per_sm_clk", "add_per_sm_clk", "sm_ghz"], [x.value for x in v]))
 
 
 def qg_version():

@@ -28,6 +28,7 @@ UNITS = [
     ("qg_propagate_cluster.cu", "qg_propagate_cluster_g8.o", ["-DQG_CLUSTER_G=8"]),
     ("qg_propagate_cluster.cu", "qg_propagate_cluster_g16.o", ["-DQG_CLUSTER_G=16"]),
     ("qg_noalloc.cu", "qg_noalloc.o", []),
+    ("qg_probe.cu", "qg_probe.o", []),
     ("qg_kernels.cu", "qg_kernels.o", []),
     ("qg_api.cu", "qg_api.o", []),
 ]

@@ -974,6 +974,11 @@ qg_status qg_batch_create(qg_state_t* states, int nstates, qg_batch_t* out) {
   if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, sizeof(InstDesc) * nstates);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_stats, sizeof(qg_step_stats) * nstates);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int) * QG_MAX_CLASSES);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int c = 0; c < b->nclass && e == cudaSuccess; ++c) {
+    e = cudaStreamCreateWithFlags(&b->cls_stream[c], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->cls_done[c], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_stats, sizeof(qg_step_stats) * nstates);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, descs.data(), sizeof(InstDesc) * nstates, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -991,6 +996,11 @@ void qg_batch_destroy(qg_batch_t b) {
   if (b->d_desc) cudaFree(b->d_desc);
   if (b->d_stats) cudaFree(b->d_stats);
   if (b->d_counter) cudaFree(b->d_counter);
+  for (int c = 0; c < QG_MAX_CLASSES; ++c) {
+    if (b->cls_stream[c]) cudaStreamDestroy(b->cls_stream[c]);
+    if (b->cls_done[c]) cudaEventDestroy(b->cls_done[c]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->h_stats) cudaFreeHost(b->h_stats);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete[] b->order;
@@ -1027,26 +1037,39 @@ static size_t class_cluster_smem(const qg_batch* b, int c, int G, int restart) {
 // for forward runs when cluster > 0, else the one-CTA form).  ninst = 0 only
 // sets function attributes.
 static cudaError_t class_launch(qg_batch* b, int c, const StepPlan& P, bool all, int ctas_per_sm, int nb_pref,
-                                int cluster) {
+                                int cluster, cudaStream_t stream) {
   const InstDesc* d = b->d_desc + b->cls_start[c];
   qg_step_stats* st = b->d_stats + b->cls_start[c];
   const int ninst = all ? b->cls_count[c] : 0;
   if (cluster > 0 && P.run == QG_RUN_FORWARD) {
     const size_t smem = class_cluster_smem(b, c, cluster, P.restart);
     if (smem == 0) return cudaErrorInvalidConfiguration;
-    return qg_launch_cluster(cluster, d, ninst, P, st, smem, b->stream);
+    return qg_launch_cluster(cluster, d, ninst, P, st, smem, stream);
   }
   return qg_launch_propagate_tuned(d, ninst, P, b->d_counter + c, st, b->cls_n[c], b->cls_S[c], ctas_per_sm, nb_pref,
-                                   b->stream);
+                                   stream);
 }
 
-// Every class, one persistent launch each, in the batch's stream.
+// Every class, one persistent launch each: a single class runs in the
+// batch's stream; several run concurrently in their own streams, forked from
+// and joined back into the batch's stream, so that one class's tail overlaps
+// the others' work.
 static cudaError_t batch_launch(qg_batch* b, const StepPlan& P, bool all) {
-  for (int c = 0; c < b->nclass; ++c) {
-    const cudaError_t e = class_launch(b, c, P, all, b->cls_ctas[c], b->cls_nb[c], b->cls_cluster[c]);
-    if (e != cudaSuccess) return e;
+  if (b->nclass == 1 || !all)
+    for (int c = 0; c < b->nclass; ++c) {
+      const cudaError_t e = class_launch(b, c, P, all, b->cls_ctas[c], b->cls_nb[c], b->cls_cluster[c], b->stream);
+      if (e != cudaSuccess) return e;
+    }
+  if (b->nclass == 1 || !all) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
+  for (int c = 0; c < b->nclass && e == cudaSuccess; ++c) {
+    e = cudaStreamWaitEvent(b->cls_stream[c], b->fork, 0);
+    if (e == cudaSuccess)
+      e = class_launch(b, c, P, all, b->cls_ctas[c], b->cls_nb[c], b->cls_cluster[c], b->cls_stream[c]);
+    if (e == cudaSuccess) e = cudaEventRecord(b->cls_done[c], b->cls_stream[c]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->cls_done[c], 0);
   }
-  return cudaSuccess;
+  return e;
 }
 
 qg_status qg_batch_run(qg_batch_t b, int method, int order, int scheme, double dt, int64_t nsteps,
@@ -1154,7 +1177,7 @@ qg_status qg_batch_autotune(qg_batch_t b, int method, int order, int scheme, dou
         continue;
       }
       e = cudaEventRecord(e0, b->stream);
-      cudaError_t el = class_launch(b, c, P, true, cand[k][0], cand[k][1], cand[k][2]);
+      cudaError_t el = class_launch(b, c, P, true, cand[k][0], cand[k][1], cand[k][2], b->stream);
       if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       if (el == cudaSuccess && e == cudaSuccess) {

@@ -187,7 +187,19 @@ struct qg_batch {
   int nclass;
   int cls_start[QG_MAX_CLASSES], cls_count[QG_MAX_CLASSES], cls_n[QG_MAX_CLASSES], cls_S[QG_MAX_CLASSES];
   int cls_ctas[QG_MAX_CLASSES], cls_nb[QG_MAX_CLASSES], cls_cluster[QG_MAX_CLASSES];
+  // the classes run concurrently: one stream per class, forked from and
+  // joined back into the batch's stream with events
+  cudaStream_t cls_stream[QG_MAX_CLASSES];
+  cudaEvent_t cls_done[QG_MAX_CLASSES];
+  cudaEvent_t fork;
 };
+
+// Raises a kernel's dynamic shared-memory limit to the device maximum, once
+// per kernel and device (thread-safe, qg_kernels.cu).  Launches of any
+// smaller size then need no further attribute call, so launches issued from
+// several host threads cannot lower the limit under one another.
+// cluster: also allow non-portable cluster sizes (more than 8 CTAs).
+cudaError_t qg_allow_max_smem(const void* fn, bool cluster = false);
 
 // Launch wrappers (qg_kernels.cu).
 size_t qg_smem_bytes(int max_n, int max_S, int restart);

@@ -4,6 +4,10 @@
 // occupancy dispatch of the persistent propagator.
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "qg_cluster.cuh"
 #include "qg_dom1d.cuh"
 
@@ -380,10 +384,31 @@ cudaError_t qg_launch_propagate(const InstDesc* d_insts, int ninst, const StepPl
   return qg_launch_propagate_tuned(d_insts, ninst, plan, d_counter, d_stats, max_n, max_S, 1, 0, st);
 }
 
+cudaError_t qg_allow_max_smem(const void* fn, bool cluster) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> hold(mu);
+  for (const auto& d : done)
+    if (d.first == fn && d.second == dev) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess && cluster) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) done.push_back({fn, dev});
+  return e;
+}
+
 cudaError_t qg_launch_apply_h(const InstDesc* d_inst, double2* d_out, int n, int S, cudaStream_t st) {
   size_t smem;
   const int nb = nb_capacity(n, S, 1, &smem);
-  cudaError_t e = cudaFuncSetAttribute(qg::apply_h_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = qg_allow_max_smem((const void*)qg::apply_h_kernel);
   if (e != cudaSuccess) return e;
   qg::apply_h_kernel<<<1, QG_THREADS, smem, st>>>(d_inst, d_out, nb);
   return cudaGetLastError();
@@ -392,7 +417,7 @@ cudaError_t qg_launch_apply_h(const InstDesc* d_inst, double2* d_out, int n, int
 cudaError_t qg_launch_energy(const InstDesc* d_inst, double* d_out, int n, int S, cudaStream_t st) {
   size_t smem;
   const int nb = nb_capacity(n, S, 1, &smem);
-  cudaError_t e = cudaFuncSetAttribute(qg::energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = qg_allow_max_smem((const void*)qg::energy_kernel);
   if (e != cudaSuccess) return e;
   qg::energy_kernel<<<1, QG_THREADS, smem, st>>>(d_inst, d_out, nb);
   return cudaGetLastError();

@@ -118,7 +118,7 @@ int qg_grid2d_ctas(const Inst2D& I) {
 }
 
 static cudaError_t coop_launch(const void* fn, int G, size_t smem, void** args, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = qg_allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   int per_sm = 0, dev = 0, sms = 0, coop = 0;
   cudaGetDevice(&dev);

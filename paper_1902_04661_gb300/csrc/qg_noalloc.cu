@@ -160,7 +160,7 @@ cudaError_t qg_noalloc_launch(int n, double qmin, double qmax, int S, double mas
   }
   size_t smem;
   const int nb = nb_capacity(n, S, P.restart, &smem);
-  e = cudaFuncSetAttribute(qg::propagate_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = qg_allow_max_smem((const void*)qg::propagate_noalloc_kernel);
   if (e != cudaSuccess) return e;
   qg::NaInstance in;
   in.n = n;

@@ -43,8 +43,7 @@ template <>
 cudaError_t qg_launch_propagate_minb<QG_MINB>(const InstDesc* d_insts, int ninst, const StepPlan& plan, int* d_counter,
                                               qg_step_stats* d_stats, int max_n, int max_S, int nb, int stage,
                                               size_t smem, int grid, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(qg::propagate_kernel<QG_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = qg_allow_max_smem((const void*)qg::propagate_kernel<QG_MINB>);
   if (e != cudaSuccess || grid == 0) return e;   // grid 0: attributes only
   qg::propagate_kernel<QG_MINB><<<grid, QG_THREADS, smem, st>>>(d_insts, ninst, plan, d_counter, d_stats, max_n,
                                                                  max_S, nb, stage);

@@ -32,12 +32,8 @@ cudaError_t qg_launch_cluster_g<QG_CLUSTER_G>(const InstDesc* d_insts, int ninst
                                               qg_step_stats* d_stats, size_t smem, cudaStream_t st) {
   constexpr int G = QG_CLUSTER_G;
   auto fn = qg::propagate_cluster_kernel<G>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = qg_allow_max_smem((const void*)fn, G > 8);
   if (e != cudaSuccess) return e;
-  if (G > 8) {
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -25,12 +25,22 @@ def test_default_start_is_euler():
     assert bench._guess(_args(guess="zero")) == 1 and bench._guess_name(_args(guess="zero")) == "zero"
 
 
-def test_traffic_only_for_the_measured_configuration():
-    assert bench._traffic(_args(), 152) == bench.NCU_TRAFFIC_BYTES
+def test_traffic_only_for_the_measured_configuration_and_sources(tmp_path, monkeypatch):
+    import json
+    rec = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", str(rec))
+    assert bench._traffic(_args(), 152) is None                      # no record
+    rec.write_text(json.dumps({"sources_sha16": bench.kernel_sources_sha16(), "dram_bytes_per_launch": 1.5e10,
+                               "surfaces_per_fft": 1}))
+    assert bench._traffic(_args(), 152) == 1.5e10
+    assert bench._traffic(_args(), 152, {"surfaces_per_fft": 1}) == 1.5e10
+    assert bench._traffic(_args(), 152, {"surfaces_per_fft": 0}) is None   # another launch shape
     assert bench._traffic(_args(precision="mixed"), 152) is None
     assert bench._traffic(_args(solver="gmres"), 152) is None
     assert bench._traffic(_args(guess="zero"), 152) is None
     assert bench._traffic(_args(), 64) is None
+    rec.write_text(json.dumps({"sources_sha16": "0" * 16, "dram_bytes_per_launch": 1.5e10}))
+    assert bench._traffic(_args(), 152) is None                      # kernel changed since the capture
 
 
 def test_flop_count_by_hand():

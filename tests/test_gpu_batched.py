@@ -89,3 +89,36 @@ def test_graph_replay_equals_direct_run(qglib, cuda):
     B.run(qglib.QG_MIDPOINT, 4, qglib.QG_SUZUKI, 0.1 * FS, 3, opts)
     for a, b in zip(a_states, b_states):
         np.testing.assert_array_equal(a.get(), b.get())
+
+
+def test_concurrent_propagate_calls_from_host_threads(qglib, cuda):
+    # one qg_propagate per model from 8 host threads on 8 streams, grid sizes
+    # mixed (each launch needs its own shared-memory size): every call
+    # succeeds and equals the same call made alone
+    import concurrent.futures as cf
+    torch = cuda
+    models = _small_models(16, nmax=8192, base=3000)
+    keep, states, refs = [], [], []
+    opts = qglib.default_solver_opts(tol=1e-13)
+    for m in models:
+        g = qglib.Grid([m["N"]], [m["qmin"]], [m["qmax"]])
+        lm = qglib.Model(g, m["S"], [m["mass"]], W=m["W"], dW=m["dW"])
+        a, b = qglib.State(lm), qglib.State(lm)
+        for s in (a, b):
+            s.set_gaussian(m["surface"], [m["q0"]], [m["p0"]], [m["sigma0"]])
+        b.propagate(qglib.QG_MIDPOINT, 4, qglib.QG_SUZUKI, 0.1 * FS, 1, opts)
+        keep += [g, lm]
+        states.append(a)
+        refs.append(b.get())
+    streams = [torch.cuda.Stream() for _ in range(8)]
+    for i, st in enumerate(states):
+        st.set_stream(streams[i % 8])
+
+    def lane(t):
+        for st in states[t::8]:
+            st.propagate(qglib.QG_MIDPOINT, 4, qglib.QG_SUZUKI, 0.1 * FS, 1, opts)
+
+    with cf.ThreadPoolExecutor(8) as ex:
+        list(ex.map(lane, range(8)))
+    for st, ref in zip(states, refs):
+        np.testing.assert_array_equal(st.get(), ref)
