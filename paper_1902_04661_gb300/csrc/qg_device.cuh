@@ -386,7 +386,7 @@ __device__ __forceinline__ R wcoupling(const R* __restrict__ F, int n, int S, in
 // pointwise symmetric W.  DOTS: also Re<x, y> and ||y||^2 (raw sums) in
 // dots[0..1].  y may alias x or z.
 template <typename R, bool DOTS>
-__device__ __forceinline__ void apply_h_diabatic(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
+__device__ __noinline__ void apply_h_diabatic(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
                                                  const typename Cx<R>::T* x, typename Cx<R>::T* y,
                                                  const typename Cx<R>::T* z, R e, R a, typename Cx<R>::T c, R* red,
                                                  R* dots) {
@@ -451,7 +451,7 @@ __device__ __forceinline__ void apply_h_diabatic(const HOp<R>& H, typename Cx<R>
 // sbuf holds nb_cap vectors of length n; H.U is scratch.  y may alias x or z.
 // z may be null when e == 0.
 template <typename R>
-__device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
+__device__ __noinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
                                               const typename Cx<R>::T* x, typename Cx<R>::T* y,
                                               const typename Cx<R>::T* z, R e, R a, typename Cx<R>::T c) {
   using C = typename Cx<R>::T;
@@ -509,7 +509,7 @@ __device__ __forceinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T
 // derivative.  DOTS: also returns the raw sums Re<x, y> and ||y||^2 in
 // dots[0..1] (one CTA reduction).  y may alias x or z.
 template <typename R, bool DOTS>
-__device__ __forceinline__ void apply_h_staged(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
+__device__ __noinline__ void apply_h_staged(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
                                                typename Cx<R>::T* sU, const typename Cx<R>::T* x,
                                                typename Cx<R>::T* y, const typename Cx<R>::T* z, R e, R a,
                                                typename Cx<R>::T c, R* red, R* dots) {

@@ -142,7 +142,7 @@ struct Dom2D {
   // and dots[1] = sum |y|^2 over the whole grid (without the grid weight),
   // reduced in the closing grid barrier; every CTA gets the same values.
   template <typename R>
-  __device__ void hpsi(const typename Cx<R>::T* x, typename Cx<R>::T* y, const typename Cx<R>::T* z, R e, R a,
+  __device__ __noinline__ void hpsi(const typename Cx<R>::T* x, typename Cx<R>::T* y, const typename Cx<R>::T* z, R e, R a,
                        typename Cx<R>::T c, R* dots = nullptr) {
     using C = typename Cx<R>::T;
     // members in registers: the stores below go through generic pointers
