@@ -35,26 +35,6 @@ int ilog2h(int v) {
   return k;
 }
 
-// Radix sequence for n = 2^k (k >= 3): as many radix-8 passes as possible,
-// the remainder as one or two radix-4 passes.
-FftPlan make_plan(int n) {
-  FftPlan p;
-  p.n = n;
-  p.npass = 0;
-  const int k = ilog2h(n);
-  int a = k / 3, rem = k % 3;
-  if (rem == 1) {
-    a -= 1;
-  }
-  for (int i = 0; i < a; ++i) p.radix[p.npass++] = 8;
-  if (rem == 2) p.radix[p.npass++] = 4;
-  if (rem == 1) {
-    p.radix[p.npass++] = 4;
-    p.radix[p.npass++] = 4;
-  }
-  return p;
-}
-
 // Twiddle table in the pass-by-pass layout fft_pass reads: for forward pass
 // i (block length L, radix R, m = L / R) the entries (r - 1) m + j,
 // r = 1..R-1, j = 0..m-1, hold w_L^{j r} = w[j r n / L] (w the natural table
@@ -86,6 +66,111 @@ void freq_positions(int len, const int* radix, int npass, std::vector<int>& f) {
   freq_positions(m, radix + 1, npass - 1, sub);
   for (int q = 0; q < R; ++q)
     for (int pp = 0; pp < m; ++pp) f[q * m + pp] = q + R * sub[pp];
+}
+
+// Accumulated frequency K of block blk of a forward pass preceded by the
+// passes radix[0..] that made nbk blocks: the block index read as
+// mixed-radix digits (first pass most significant), digits reversed.
+int block_frequency(int blk, const int* radix, int nbk) {
+  int K = 0, mult = 1, rem = blk, size = nbk, i = 0;
+  while (size > 1) {
+    const int R = radix[i++];
+    size /= R;
+    const int d = rem / size;
+    rem -= d * size;
+    K += d * mult;
+    mult *= R;
+  }
+  return K;
+}
+
+// w = exp(sgn 2 pi i num / den) in Linzer and Feig's factored form: w = s (1
+// + i t) (form 0, |Re w| >= |Im w|) or w = s (t + i) (form 1), so |t| <= 1.
+// cos and sin are evaluated in long double on at most an eighth of a turn
+// and rotated by an exact multiple of a quarter turn; t is divided out in
+// long double before rounding.
+void lf_factor(long long num, long long den, int sgn, double2* st, unsigned* form) {
+  num %= den;
+  if (num < 0) num += den;
+  const long long q = (4 * num + den / 2) / den;   // nearest quarter turn
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  const long double a = two_pi * (long double)(4 * num - q * den) / (4.0L * (long double)den);
+  long double c = cosl(a), s = sinl(a);
+  for (long long r = 0; r < (q & 3); ++r) {   // times i
+    const long double t = c;
+    c = -s;
+    s = t;
+  }
+  if (sgn < 0) s = -s;
+  if (fabsl(c) >= fabsl(s)) {
+    *st = make_double2((double)c, (double)(s / c));
+    *form = 0u;
+  } else {
+    *st = make_double2((double)s, (double)(c / s));
+    *form = 1u;
+  }
+}
+
+// Factor tables of the FP64 transform's Linzer-Feig passes, in the order the
+// device runs them.  Forward passes 1..npass-1 (decimation in frequency with
+// the twiddles taken at the input of a pass): block blk of a pass of radix R
+// with nbk blocks multiplies its input r by W^r, W = exp(-2 pi i K / (nbk R)),
+// K = block_frequency(blk).  Inverse passes npass-2..0 (decimation in time):
+// position j of a pass with block length L multiplies input r by W^r, W =
+// exp(+2 pi i j / L).  A radix-8 set holds W^4, W^2, W and zeta W (zeta =
+// exp(-+2 pi i / 8), the sign of the pass), a radix-4 set W^2 and W; entry e
+// of set k of a pass sits at e * nsets + k.  flg gets one word per set, bit e
+// the form of entry e, in the same set order.
+void lf_tables(const FftPlan& p, std::vector<double2>& ent, std::vector<unsigned>& flg) {
+  const int n = p.n, np = p.npass;
+  int Ls[QG_MAX_PASSES];
+  for (int i = 0, L = n; i < np; ++i) {
+    Ls[i] = L;
+    L /= p.radix[i];
+  }
+  ent.clear();
+  flg.clear();
+  // one pass: nsets sets of E entries, set k's exponents num[e] / den[e]
+  auto pass = [&](int R, int nsets, int sgn, auto&& exps) {
+    const int E = R == 8 ? 4 : 2;
+    const size_t base = ent.size(), fbase = flg.size();
+    ent.resize(base + (size_t)E * nsets);
+    flg.resize(fbase + nsets, 0u);
+    for (int k = 0; k < nsets; ++k) {
+      long long num[4], den[4];
+      exps(k, num, den);
+      for (int e = 0; e < E; ++e) {
+        unsigned f = 0;
+        lf_factor(num[e], den[e], sgn, &ent[base + (size_t)e * nsets + k], &f);
+        flg[fbase + k] |= f << e;
+      }
+    }
+  };
+  for (int i = 1; i < np; ++i) {
+    const int R = p.radix[i], nbk = n / Ls[i];
+    const long long B = (long long)nbk * R;
+    pass(R, nbk, -1, [&](int blk, long long* num, long long* den) {
+      const long long K = block_frequency(blk, p.radix, nbk);
+      const long long a[4] = {4 * K, 2 * K, K, 8 * K + B}, b[4] = {B, B, B, 8 * B};
+      const int o = R == 8 ? 0 : 1;   // radix 4: W^2, W
+      for (int e = 0; e + o < 4; ++e) {
+        num[e] = a[e + o];
+        den[e] = b[e + o];
+      }
+    });
+  }
+  for (int i = np - 2; i >= 0; --i) {
+    const int R = p.radix[i];
+    const long long L = Ls[i];
+    pass(R, Ls[i] / R, +1, [&](int j, long long* num, long long* den) {
+      const long long a[4] = {4LL * j, 2LL * j, (long long)j, 8LL * j + L}, b[4] = {L, L, L, 8 * L};
+      const int o = R == 8 ? 0 : 1;
+      for (int e = 0; e + o < 4; ++e) {
+        num[e] = a[e + o];
+        den[e] = b[e + o];
+      }
+    });
+  }
 }
 
 // exp(-2 pi i k / n) for k = 0..n-1.  cos/sin are evaluated in long double
@@ -223,6 +308,8 @@ InstDesc make_desc(const qg_state* s) {
   d.dq = g->dq[0];
   d.tw = g->d_tw[0];
   d.kd = g->d_kd[0];
+  d.lf = g->d_lf[0];
+  d.lff = g->d_lff[0];
   d.V = m->d_V;
   d.F = m->d_F;
   d.psi = s->d_psi;
@@ -364,7 +451,18 @@ qg_status qg_create_grid(int D, const int* N, const double* qmin, const double* 
       tw32[p] = make_float2((float)tw[p].x, (float)tw[p].y);
       kd32[p] = (float)kd[p];
     }
+    std::vector<double2> lfe;
+    std::vector<unsigned> lff;
+    lf_tables(g->plan[d], lfe, lff);
+    const size_t lf_bytes = lf_table_bytes(n);
     cudaError_t e = cudaMalloc(&g->d_tw[d], sizeof(double2) * n);
+    if (e == cudaSuccess && lf_bytes > 0) e = cudaMalloc(&g->d_lf[d], lf_bytes);
+    if (e == cudaSuccess && lf_bytes > 0) {
+      g->d_lff[d] = reinterpret_cast<unsigned*>(g->d_lf[d] + lfe.size());
+      e = cudaMemcpy(g->d_lf[d], lfe.data(), sizeof(double2) * lfe.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(g->d_lff[d], lff.data(), sizeof(unsigned) * lff.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&g->d_kd[d], sizeof(double) * n);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_tw32[d], sizeof(float2) * n);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_kd32[d], sizeof(float) * n);
@@ -386,6 +484,7 @@ void qg_destroy_grid(qg_grid_t g) {
   if (!g) return;
   for (int d = 0; d < 2; ++d) {
     if (g->d_tw[d]) cudaFree(g->d_tw[d]);
+    if (g->d_lf[d]) cudaFree(g->d_lf[d]);
     if (g->d_kd[d]) cudaFree(g->d_kd[d]);
     if (g->d_tw32[d]) cudaFree(g->d_tw32[d]);
     if (g->d_kd32[d]) cudaFree(g->d_kd32[d]);

@@ -172,24 +172,26 @@ __device__ __forceinline__ void dft8(C (&x)[8]) {
   C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
   dft4<INV>(e0, e1, e2, e3);
   dft4<INV>(o0, o1, o2, o3);
+  // o1 and o3 times (+-1 +- i) / sqrt2: the sums and differences of their
+  // parts, the 1/sqrt2 folded into the fused multiply-adds below
   C t1, t2, t3;
   if (!INV) {
-    t1 = cmk<C>((o1.x + o1.y) * r2, (o1.y - o1.x) * r2);     // (1 - i)/sqrt2
-    t2 = cmk<C>(o2.y, -o2.x);                                 // -i
-    t3 = cmk<C>((o3.y - o3.x) * r2, -(o3.x + o3.y) * r2);    // (-1 - i)/sqrt2
+    t1 = cmk<C>(o1.x + o1.y, o1.y - o1.x);     // (1 - i) o1
+    t2 = cmk<C>(o2.y, -o2.x);                  // -i o2
+    t3 = cmk<C>(o3.y - o3.x, -(o3.x + o3.y));  // (-1 - i) o3
   } else {
-    t1 = cmk<C>((o1.x - o1.y) * r2, (o1.x + o1.y) * r2);     // (1 + i)/sqrt2
-    t2 = cmk<C>(-o2.y, o2.x);                                 // i
-    t3 = cmk<C>(-(o3.x + o3.y) * r2, (o3.x - o3.y) * r2);    // (-1 + i)/sqrt2
+    t1 = cmk<C>(o1.x - o1.y, o1.x + o1.y);     // (1 + i) o1
+    t2 = cmk<C>(-o2.y, o2.x);                  // i o2
+    t3 = cmk<C>(-(o3.x + o3.y), o3.x - o3.y);  // (-1 + i) o3
   }
   x[0] = cadd(e0, o0);
   x[4] = csub(e0, o0);
-  x[1] = cadd(e1, t1);
-  x[5] = csub(e1, t1);
+  x[1] = caxpy_r(r2, t1, e1);
+  x[5] = caxpy_r(-r2, t1, e1);
   x[2] = cadd(e2, t2);
   x[6] = csub(e2, t2);
-  x[3] = cadd(e3, t3);
-  x[7] = csub(e3, t3);
+  x[3] = caxpy_r(r2, t3, e3);
+  x[7] = caxpy_r(-r2, t3, e3);
 }
 
 template <int RD, bool INV, typename C>
@@ -218,6 +220,11 @@ struct HOp {
   C* U;          // scratch vector (S * n)
   int diab;      // 1: the diabatic representation, H = -hbar^2/2m D^2 + W, with
                  // V = diag W and F = the upper triangle of W (symmetric)
+  // FP64 only: Linzer-Feig factor tables (entries, form words; see
+  // lf_derivative), or null -- the transform then runs the passes of
+  // fft_pass with the twiddles tw
+  const double2* lf = nullptr;
+  const unsigned* lff = nullptr;
 };
 
 // Number of leading radix-8 passes of a plan.
@@ -312,6 +319,224 @@ __device__ __forceinline__ void fft_center(C* gbuf, int n, int nb, const R* __re
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 transform in Linzer and Feig's fused multiply-add form.  A twiddle
+// factored as w = s (1 + i t) (form 0, |Re w| >= |Im w|) or w = s (t + i)
+// (form 1), |t| <= 1, turns the radix-2 step (a, b) -> (a + w b, a - w b)
+// into six fused multiply-adds: u = b (1 + i t) or b (t + i) in two, then a
+// +- s u in four.  A radix-R step with input twiddles W^r (r = 0..R-1) is
+// log2 R levels of such steps whose factors are W^(R/2), W^(R/4), ..., and
+// their products with the R-th roots of unity; a product with -i (forward) or
+// +i (inverse) changes only the form, the sign of t and the roles of the
+// parts of s, so a radix-8 set stores W^4, W^2, W and zeta W, a radix-4 set
+// W^2 and W.  The forward transform is the decimation-in-frequency sequence
+// of fft_pass with each pass's twiddles moved to the input of the next pass:
+// block blk of pass i then multiplies its inputs by W^r with W a root of
+// unity of order (blocks x radix), indexed by the frequency the block has
+// accumulated (the first pass has none).  The inverse is the
+// decimation-in-time sequence, whose twiddles already sit at the input.
+// Outputs of a step leave in bit-reversed register order.
+
+// One factor: x and y multipliers of the a +- s u update (sx = -s for form
+// 1, whose u is computed with its real part negated), t and the form.
+struct LfW {
+  double sx, sy, t;
+  bool f;
+};
+
+__device__ __forceinline__ LfW lf_w(double2 st, bool f) { return LfW{f ? -st.x : st.x, st.x, st.y, f}; }
+
+// The factor of -i w (forward) or +i w (inverse).
+template <bool INV>
+__device__ __forceinline__ LfW lf_rot(const LfW& w) {
+  return INV ? LfW{-w.sy, w.sx, -w.t, !w.f} : LfW{w.sy, -w.sx, -w.t, !w.f};
+}
+
+// (a, b) <- (a + w b, a - w b).
+__device__ __forceinline__ void lf2(double2& a, double2& b, const LfW& w) {
+  const double p = w.f ? b.y : b.x;
+  const double q = w.f ? b.x : b.y;
+  const double ux = fma(-w.t, q, p);   // form 0: Re b (1 + i t); form 1: -Re b (t + i)
+  const double uy = fma(w.t, p, q);    // Im of the same product
+  const double2 a0 = a;
+  a = make_double2(fma(w.sx, ux, a0.x), fma(w.sy, uy, a0.y));
+  b = make_double2(fma(-w.sx, ux, a0.x), fma(-w.sy, uy, a0.y));
+}
+
+// Radix-RD DFT of x_r W^r (forward) or its inverse counterpart, w[] the
+// stored factors (W^4, W^2, W, zeta W or W^2, W); x[s] receives output
+// bitrev(s).
+template <int RD, bool INV>
+__device__ __forceinline__ void lf_bfly(double2 (&x)[RD], const LfW (&w)[RD == 8 ? 4 : 2]) {
+  if constexpr (RD == 8) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) lf2(x[r], x[r + 4], w[0]);
+    const LfW w2r = lf_rot<INV>(w[1]);
+    lf2(x[0], x[2], w[1]);
+    lf2(x[1], x[3], w[1]);
+    lf2(x[4], x[6], w2r);
+    lf2(x[5], x[7], w2r);
+    lf2(x[0], x[1], w[2]);
+    lf2(x[2], x[3], lf_rot<INV>(w[2]));
+    lf2(x[4], x[5], w[3]);
+    lf2(x[6], x[7], lf_rot<INV>(w[3]));
+  } else {
+    lf2(x[0], x[2], w[0]);
+    lf2(x[1], x[3], w[0]);
+    lf2(x[0], x[1], w[1]);
+    lf2(x[2], x[3], lf_rot<INV>(w[1]));
+  }
+}
+
+template <int RD>
+__device__ __forceinline__ int bitrev(int s) {
+  return RD == 8 ? ((s & 1) << 2) | (s & 2) | (s >> 2) : ((s & 1) << 1) | (s >> 1);
+}
+
+// Set k of a pass with nsets sets (entries e * nsets + k, form word k).
+template <int RD>
+__device__ __forceinline__ void lf_load(const double2* __restrict__ ent, const unsigned* __restrict__ flg, int nsets,
+                                        int k, LfW (&w)[RD == 8 ? 4 : 2]) {
+  const unsigned fl = flg[k];
+#pragma unroll
+  for (int e = 0; e < (RD == 8 ? 4 : 2); ++e) w[e] = lf_w(ent[e * nsets + k], (fl >> e) & 1u);
+}
+
+// One radix-RD pass over nb vectors in shared memory, the element layout of
+// fft_pass (block length L, m = L / RD, elements j + r m of a block).  TW =
+// false: the untwiddled first forward pass (plain DFT; src as in fft_pass);
+// TW = true: the factored step with set blk (forward) or j (inverse) of the
+// pass's tables.
+template <int RD, bool INV, bool TW>
+__device__ __forceinline__ void lf_pass(double2* gbuf, int n, int nb, int L, const double2* __restrict__ ent,
+                                        const unsigned* __restrict__ flg, const double2* src = nullptr) {
+  double2* buf = in_dyn_smem(gbuf);
+  const int lm = ilog2(L / RD);
+  const int m = 1 << lm;
+  const int lpv = ilog2(n / RD);
+  const int total = nb << lpv;
+  const int nsets = INV ? m : n / L;
+  for (int b = threadIdx.x; b < total; b += kThreads) {
+    const int v = b >> lpv;
+    const int bb = b & ((n / RD) - 1);
+    const int blk = bb >> lm;
+    const int j = bb & (m - 1);
+    const int e0 = v * n + blk * L + j;
+    double2 x[RD];
+    if (src) {
+#pragma unroll
+      for (int r = 0; r < RD; ++r) x[r] = src[e0 + r * m];
+    } else {
+#pragma unroll
+      for (int r = 0; r < RD; ++r) x[r] = buf[spad<double2>(e0 + r * m)];
+    }
+    if constexpr (!TW) {
+      dft<RD, INV>(x);
+#pragma unroll
+      for (int r = 0; r < RD; ++r) buf[spad<double2>(e0 + r * m)] = x[r];
+    } else {
+      LfW w[RD == 8 ? 4 : 2];
+      lf_load<RD>(ent, flg, nsets, INV ? j : blk, w);
+      lf_bfly<RD, INV>(x, w);
+#pragma unroll
+      for (int s = 0; s < RD; ++s) buf[spad<double2>(e0 + bitrev<RD>(s) * m)] = x[s];
+    }
+  }
+}
+
+// Last forward pass (block length RD; factored with set blk when TW), times
+// i k / n (second: -n (k/n)^2), first inverse pass (untwiddled) -- in
+// registers, as fft_center.
+template <int RD, bool TW>
+__device__ __forceinline__ void lf_center(double2* gbuf, int n, int nb, const double* __restrict__ kd,
+                                          const double2* __restrict__ ent, const unsigned* __restrict__ flg,
+                                          int second) {
+  double2* buf = in_dyn_smem(gbuf);
+  const int total = (nb * n) / RD;
+  const double mn = -(double)n;
+  for (int b = threadIdx.x; b < total; b += kThreads) {
+    const int e0 = b * RD;
+    const int pos = e0 & (n - 1);
+    double2 x[RD], y[RD];
+#pragma unroll
+    for (int r = 0; r < RD; ++r) x[r] = buf[spad<double2>(e0 + r)];
+    if constexpr (TW) {
+      LfW w[RD == 8 ? 4 : 2];
+      lf_load<RD>(ent, flg, n / RD, pos / RD, w);
+      lf_bfly<RD, false>(x, w);
+#pragma unroll
+      for (int k = 0; k < RD; ++k) y[k] = x[bitrev<RD>(k)];
+    } else {
+      dft<RD, false>(x);
+#pragma unroll
+      for (int k = 0; k < RD; ++k) y[k] = x[k];
+    }
+    if (second) {
+#pragma unroll
+      for (int k = 0; k < RD; ++k) {
+        const double q = kd[pos + k];
+        y[k] = cscale(mn * q * q, y[k]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < RD; ++k) {
+        const double q = kd[pos + k];
+        y[k] = make_double2(-q * y[k].y, q * y[k].x);
+      }
+    }
+    dft<RD, true>(y);
+#pragma unroll
+    for (int r = 0; r < RD; ++r) buf[spad<double2>(e0 + r)] = y[r];
+  }
+}
+
+// spectral_derivative's FP64 transform with the factored passes; the tables
+// run forward passes 1..np-1, then inverse passes np-2..0 (lf_tables).
+__device__ __forceinline__ void lf_derivative(double2* buf, int nb, const HOp<double>& H, const double2* src,
+                                              int second) {
+  const int n = H.n, np = H.npass, n8 = H.n8;
+  const double* kd = H.kd;
+  const double2* ent = H.lf;
+  const unsigned* flg = H.lff;
+  int L = n;
+  for (int i = 0; i < np - 1; ++i) {
+    const int RD = i < n8 ? 8 : 4;
+    if (i == 0) {
+      if (RD == 8)
+        lf_pass<8, false, false>(buf, n, nb, L, nullptr, nullptr, src);
+      else
+        lf_pass<4, false, false>(buf, n, nb, L, nullptr, nullptr, src);
+    } else {
+      if (RD == 8)
+        lf_pass<8, false, true>(buf, n, nb, L, ent, flg);
+      else
+        lf_pass<4, false, true>(buf, n, nb, L, ent, flg);
+      ent += (RD == 8 ? 4 : 2) * (n / L);
+      flg += n / L;
+    }
+    L /= RD;
+    __syncthreads();
+  }
+  if (np - 1 < n8)
+    lf_center<8, true>(buf, n, nb, kd, ent, flg, second);
+  else
+    lf_center<4, true>(buf, n, nb, kd, ent, flg, second);
+  ent += (L == 8 ? 4 : 2) * (n / L);
+  flg += n / L;
+  __syncthreads();
+  for (int i = np - 2; i >= 0; --i) {
+    const int RD = i < n8 ? 8 : 4;
+    L *= RD;
+    if (RD == 8)
+      lf_pass<8, true, true>(buf, n, nb, L, ent, flg);
+    else
+      lf_pass<4, true, true>(buf, n, nb, L, ent, flg);
+    ent += (RD == 8 ? 4 : 2) * (L / RD);
+    flg += L / RD;
+    __syncthreads();
+  }
+}
+
 // buf <- D buf for nb vectors (spectral first derivative, Sec. II D):
 // forward FFT, multiply by i k, inverse FFT (1/n folded into kd).
 // One out-of-line copy per precision: its call sites share the code (fewer
@@ -326,6 +551,12 @@ __device__ __noinline__ void spectral_derivative(typename Cx<R>::T* buf, int nb,
   const int n = H.n, np = H.npass, n8 = H.n8;
   const C* tw = H.tw;
   const R* kd = H.kd;
+  if constexpr (sizeof(R) == 8) {
+    if (H.lf && np >= 2) {
+      lf_derivative(buf, nb, H, src, second);
+      return;
+    }
+  }
   if (src && np == 1) {   // no twiddled pass to fuse the copy into
     C* sb = in_dyn_smem(buf);
     for (int i = threadIdx.x; i < nb * n; i += kThreads) sb[spad<C>(i)] = src[i];

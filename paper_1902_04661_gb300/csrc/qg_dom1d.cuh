@@ -12,8 +12,9 @@ namespace qg {
 // max_n complex doubles, also used by the FP32 passes), then the GMRES arrays
 // sized for doubles (the FP32 arrays fit in the same space).
 // Optional staging regions follow (flags of the launch, see stage_plan):
-// kStageTables -- the instance's FP64 twiddles and wave numbers (max_n
-// double2 + max_n double), so the FFT passes read them from shared memory;
+// kStageTables -- the instance's FP64 transform tables (the Linzer-Feig
+// factors, lf_table_bytes(max_n), and max_n wave numbers), so the FFT passes
+// read them from shared memory;
 // kStageU -- the intermediate U = (D + F) x of H psi (max_S x max_n double2),
 // so H psi makes fewer passes over global memory.
 enum { kStageTables = 1, kStageU = 2 };
@@ -21,7 +22,7 @@ enum { kStageTables = 1, kStageU = 2 };
 struct Smem {
   unsigned char* fft;
   unsigned char* gm;
-  double2* tw;   // staged twiddles or null
+  unsigned char* lf;   // staged factor tables (entries, then form words) or null
   double* kd;    // staged wave numbers or null
   double2* su;   // staged U or null
   int nb_cap;
@@ -30,6 +31,12 @@ struct Smem {
 
 __host__ __device__ inline size_t gm_region_bytes(int m) { return (gmres_smem_bytes(m) + 255) & ~size_t(255); }
 
+// The kStageTables region: factor tables, then wave numbers.
+__host__ __device__ inline size_t lf_region_bytes(int max_n) { return (lf_table_bytes(max_n) + 255) & ~size_t(255); }
+__host__ __device__ inline size_t table_region_bytes(int max_n) {
+  return lf_region_bytes(max_n) + (((size_t)max_n * sizeof(double) + 255) & ~size_t(255));
+}
+
 static __device__ Smem carve_smem(void* base, int max_n, int nb_cap, int m, int stage = 0, int max_S = 0) {
   Smem s;
   unsigned char* p = reinterpret_cast<unsigned char*>(base);
@@ -37,14 +44,13 @@ static __device__ Smem carve_smem(void* base, int max_n, int nb_cap, int m, int 
   p += (padded_bytes((size_t)nb_cap * max_n, sizeof(double2)) + 255) & ~size_t(255);
   s.gm = p;
   p += gm_region_bytes(m);
-  s.tw = nullptr;
+  s.lf = nullptr;
   s.kd = nullptr;
   s.su = nullptr;
   if (stage & kStageTables) {
-    s.tw = reinterpret_cast<double2*>(p);
-    p += (size_t)max_n * sizeof(double2);
-    s.kd = reinterpret_cast<double*>(p);
-    p += ((size_t)max_n * sizeof(double) + 255) & ~size_t(255);
+    s.lf = p;
+    s.kd = reinterpret_cast<double*>(p + lf_region_bytes(max_n));
+    p += table_region_bytes(max_n);
   }
   if (stage & kStageU) s.su = reinterpret_cast<double2*>(p);
   s.nb_cap = nb_cap;
@@ -62,6 +68,8 @@ __device__ __forceinline__ HOp<double> hop64(const InstDesc& I, double2* U) {
   H.h2m = I.h2m;
   H.tw = I.tw;
   H.kd = I.kd;
+  H.lf = I.lf;
+  H.lff = I.lff;
   H.V = I.V;
   H.F = I.F;
   H.U = U;
@@ -161,8 +169,8 @@ struct Dom1D {
   __device__ __forceinline__ bool ok() const { return true; }
 };
 
-// The instance's H psi operands; with kStageTables the FP64 twiddles and
-// wave numbers are first copied into shared memory.
+// The instance's H psi operands; with kStageTables the FP64 factor tables
+// and wave numbers are first copied into shared memory.
 static __device__ Dom1D make_dom1d(const InstDesc& I, const Smem& sm, int m, double* red) {
   const int len = I.S * I.n;
   Dom1D D;
@@ -171,14 +179,20 @@ static __device__ Dom1D make_dom1d(const InstDesc& I, const Smem& sm, int m, dou
   D.gm = sm.gm;
   D.red = red;
   D.H64 = hop64(I, I.work);
-  if (sm.tw) {
-    for (int k = threadIdx.x; k < I.n; k += kThreads) {
-      sm.tw[k] = I.tw[k];
-      sm.kd[k] = I.kd[k];
+  if (sm.kd) {
+    for (int k = threadIdx.x; k < I.n; k += kThreads) sm.kd[k] = I.kd[k];
+    D.H64.kd = sm.kd;
+    if (I.lf) {
+      // entries and form words are one block of whole 16-byte words
+      const int words = (int)(lf_table_bytes(I.n) / 16);
+      const int4* src = reinterpret_cast<const int4*>(I.lf);
+      int4* dst = reinterpret_cast<int4*>(sm.lf);
+      for (int k = threadIdx.x; k < words; k += kThreads) dst[k] = src[k];
+      D.H64.lf = reinterpret_cast<const double2*>(sm.lf);
+      D.H64.lff = reinterpret_cast<const unsigned*>(sm.lf + (reinterpret_cast<const unsigned char*>(I.lff) -
+                                                             reinterpret_cast<const unsigned char*>(I.lf)));
     }
     __syncthreads();
-    D.H64.tw = sm.tw;
-    D.H64.kd = sm.kd;
   }
   D.su = sm.su;
   D.fb = sm.fft;
@@ -319,7 +333,7 @@ static inline int nb_capacity(int max_n, int max_S, int restart, size_t* bytes_o
 // first, then U.
 static inline int stage_plan(int max_n, int max_S, size_t budget, size_t* bytes) {
   int stage = 0;
-  const size_t tab = (size_t)max_n * 16 + (((size_t)max_n * 8 + 255) & ~size_t(255));
+  const size_t tab = qg::table_region_bytes(max_n);
   if (*bytes + tab <= budget) {
     stage |= qg::kStageTables;
     *bytes += tab;

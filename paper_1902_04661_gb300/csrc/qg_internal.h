@@ -30,6 +30,57 @@ struct FftPlan {
   int radix[QG_MAX_PASSES];
 };
 
+// Radix sequence for n = 2^k (k >= 2): as many radix-8 passes as possible,
+// the remainder as one or two radix-4 passes.
+__host__ __device__ inline FftPlan make_plan(int n) {
+  FftPlan p;
+  p.n = n;
+  p.npass = 0;
+  int k = 0;
+  while ((1 << k) < n) ++k;
+  int a = k / 3;
+  const int rem = k % 3;
+  if (rem == 1) a -= 1;
+  for (int i = 0; i < a; ++i) p.radix[p.npass++] = 8;
+  if (rem == 2) p.radix[p.npass++] = 4;
+  if (rem == 1) {
+    p.radix[p.npass++] = 4;
+    p.radix[p.npass++] = 4;
+  }
+  return p;
+}
+
+// Sizes of the Linzer-Feig factor tables of the FP64 transform of a plan
+// (qg_api.cu, lf_tables): one set of factors per block of forward passes
+// 1..npass-1 and per position of inverse passes 0..npass-2, 4 double2
+// entries per radix-8 set and 2 per radix-4 set, one word of form bits per
+// set.
+__host__ __device__ inline void lf_counts(const int* radix, int npass, int n, int* entries, int* sets) {
+  int e = 0, s = 0, L = n;
+  for (int i = 0; i < npass; ++i) {
+    const int R = radix[i], E = R == 8 ? 4 : 2;
+    if (i >= 1) {
+      e += E * (n / L);
+      s += n / L;
+    }
+    if (i <= npass - 2) {
+      e += E * (L / R);
+      s += L / R;
+    }
+    L /= R;
+  }
+  *entries = e;
+  *sets = s;
+}
+
+// Bytes of those tables for n points (entries, then form words, padded to 16).
+__host__ __device__ inline size_t lf_table_bytes(int n) {
+  const FftPlan p = make_plan(n);
+  int e = 0, s = 0;
+  lf_counts(p.radix, p.npass, n, &e, &s);
+  return ((size_t)e * 16 + (size_t)s * 4 + 15) & ~(size_t)15;
+}
+
 struct qg_grid {
   int D;
   int n[2];
@@ -37,6 +88,8 @@ struct qg_grid {
   int ntot;
   FftPlan plan[2];
   double2* d_tw[2];  // tw[k] = exp(-2 pi i k / n), k = 0..n-1
+  double2* d_lf[2];  // Linzer-Feig factor tables of the FP64 transform (entries, then the form words)
+  unsigned* d_lff[2];  // the form words (inside the d_lf allocation)
   double* d_kd[2];   // k of the frequency held at digit-reversed position p, divided by n
   float2* d_tw32[2];  // the same tables rounded to FP32 (mixed-precision inner solves)
   float* d_kd32[2];
@@ -96,6 +149,8 @@ struct InstDesc {
   double dq;
   const double2* tw;
   const double* kd;
+  const double2* lf;     // Linzer-Feig factor tables (FP64 transform), or null: the
+  const unsigned* lff;   // transform then runs its twiddle passes from tw
   const double* V;
   const double* F;
   double2* psi;

@@ -94,6 +94,8 @@ __global__ void __launch_bounds__(QG_THREADS, 1)
   I.dq = in.dq;
   I.tw = reinterpret_cast<const double2*>(base + kNaWorkBytes);
   I.kd = reinterpret_cast<const double*>(base + kNaWorkBytes + kNaTwBytes);
+  I.lf = nullptr;   // the transforms run their twiddle passes from tw
+  I.lff = nullptr;
   I.V = in.V;
   I.F = in.F;
   I.psi = in.psi;
