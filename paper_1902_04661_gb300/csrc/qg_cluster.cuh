@@ -185,6 +185,10 @@ struct DomC {
     const int n = len;
     for (int i = threadIdx.x; i < n; i += kThreads) f(i);
   }
+  template <int U, class Ld, class St>
+  __device__ __forceinline__ void each_u(Ld&& ld, St&& st) {
+    each([&](int i) { st(i, ld(i)); });
+  }
 
   template <int K, typename R>
   __device__ __forceinline__ bool sum(R (&v)[K], R* out) {

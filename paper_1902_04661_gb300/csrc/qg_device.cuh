@@ -78,6 +78,16 @@ __device__ __forceinline__ C cnaxpy(C c, C b, C a) {
 template <typename C>
 __device__ __forceinline__ C mul_i(C a) { return cmk<C>(-a.y, a.x); }
 
+// -x when neg, else x, by flipping the sign bit with an integer operation: a
+// data-dependent choice between x and -x would otherwise cost a floating-point
+// negation (an FP64 add, on the FP64 pipe, for doubles).
+__device__ __forceinline__ double neg_if(double x, bool neg) {
+  return __hiloint2double(__double2hiint(x) ^ (neg ? (int)0x80000000 : 0), __double2loint(x));
+}
+__device__ __forceinline__ float neg_if(float x, bool neg) {
+  return __int_as_float(__float_as_int(x) ^ (neg ? (int)0x80000000 : 0));
+}
+
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 
 // Shared-memory FFT buffers are padded with one element after every 8
@@ -149,9 +159,10 @@ __device__ __forceinline__ void dft2(C& a, C& b) {
   b = csub(t, b);
 }
 
+// The radix-4 DFT after its first level: a = x0 + x2, b = x0 - x2, c = x1 +
+// x3, d = x1 - x3 given; outputs in x0..x3.
 template <bool INV, typename C>
-__device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
-  C a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
+__device__ __forceinline__ void dft4_rest(C a, C b, C c, C d, C& x0, C& x1, C& x2, C& x3) {
   C id = mul_i(d);
   x0 = cadd(a, c);
   x2 = csub(a, c);
@@ -165,13 +176,19 @@ __device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
 }
 
 template <bool INV, typename C>
-__device__ __forceinline__ void dft8(C (&x)[8]) {
+__device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
+  dft4_rest<INV>(cadd(x0, x2), csub(x0, x2), cadd(x1, x3), csub(x1, x3), x0, x1, x2, x3);
+}
+
+// The radix-8 DFT after its first level: p[k] = x_k + x_{k+4}, q[k] = x_k -
+// x_{k+4} (k < 4) given; outputs in x.
+template <bool INV, typename C>
+__device__ __forceinline__ void dft8_rest(const C (&p)[4], const C (&q)[4], C (&x)[8]) {
   using R = decltype(C::x);
   const R r2 = (R)0.70710678118654752440;
-  C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
-  C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
-  dft4<INV>(e0, e1, e2, e3);
-  dft4<INV>(o0, o1, o2, o3);
+  C e0, e1, e2, e3, o0, o1, o2, o3;
+  dft4_rest<INV>(p[0], q[0], p[2], q[2], e0, e1, e2, e3);   // even inputs
+  dft4_rest<INV>(p[1], q[1], p[3], q[3], o0, o1, o2, o3);   // odd inputs
   // o1 and o3 times (+-1 +- i) / sqrt2: the sums and differences of their
   // parts, the 1/sqrt2 folded into the fused multiply-adds below
   C t1, t2, t3;
@@ -192,6 +209,17 @@ __device__ __forceinline__ void dft8(C (&x)[8]) {
   x[6] = csub(e2, t2);
   x[3] = caxpy_r(r2, t3, e3);
   x[7] = caxpy_r(-r2, t3, e3);
+}
+
+template <bool INV, typename C>
+__device__ __forceinline__ void dft8(C (&x)[8]) {
+  C p[4], q[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    p[k] = cadd(x[k], x[k + 4]);
+    q[k] = csub(x[k], x[k + 4]);
+  }
+  dft8_rest<INV>(p, q, x);
 }
 
 template <int RD, bool INV, typename C>
@@ -344,7 +372,7 @@ struct LfW {
   bool f;
 };
 
-__device__ __forceinline__ LfW lf_w(double2 st, bool f) { return LfW{f ? -st.x : st.x, st.x, st.y, f}; }
+__device__ __forceinline__ LfW lf_w(double2 st, bool f) { return LfW{neg_if(st.x, f), st.x, st.y, f}; }
 
 // The factor of -i w (forward) or +i w (inverse).
 template <bool INV>
@@ -447,10 +475,9 @@ __device__ __forceinline__ void lf_pass(double2* gbuf, int n, int nb, int L, con
 // Last forward pass (block length RD; factored with set blk when TW), times
 // i k / n (second: -n (k/n)^2), first inverse pass (untwiddled) -- in
 // registers, as fft_center.
-template <int RD, bool TW>
+template <int RD, bool TW, bool SECOND>
 __device__ __forceinline__ void lf_center(double2* gbuf, int n, int nb, const double* __restrict__ kd,
-                                          const double2* __restrict__ ent, const unsigned* __restrict__ flg,
-                                          int second) {
+                                          const double2* __restrict__ ent, const unsigned* __restrict__ flg) {
   double2* buf = in_dyn_smem(gbuf);
   const int total = (nb * n) / RD;
   const double mn = -(double)n;
@@ -471,20 +498,28 @@ __device__ __forceinline__ void lf_center(double2* gbuf, int n, int nb, const do
 #pragma unroll
       for (int k = 0; k < RD; ++k) y[k] = x[k];
     }
-    if (second) {
+    // the spectral multiplier w_k (i k / n, or -n (k/n)^2) fused into the
+    // first level of the inverse DFT: w_k y_k +- w_{k+h} y_{k+h}, h = RD / 2,
+    // as one multiply and two fused multiply-adds per part
+    constexpr int h = RD / 2;
+    double2 p[h], q[h];
 #pragma unroll
-      for (int k = 0; k < RD; ++k) {
-        const double q = kd[pos + k];
-        y[k] = cscale(mn * q * q, y[k]);
+    for (int k = 0; k < h; ++k) {
+      double w0 = kd[pos + k], w1 = kd[pos + k + h];
+      if (SECOND) {
+        w0 *= mn * w0;
+        w1 *= mn * w1;
       }
-    } else {
-#pragma unroll
-      for (int k = 0; k < RD; ++k) {
-        const double q = kd[pos + k];
-        y[k] = make_double2(-q * y[k].y, q * y[k].x);
-      }
+      const double2 t = make_double2(w0 * y[k].x, w0 * y[k].y);
+      const double2 sp = caxpy_r(w1, y[k + h], t), sm = caxpy_r(-w1, y[k + h], t);
+      p[k] = SECOND ? sp : mul_i(sp);   // i k: times i
+      q[k] = SECOND ? sm : mul_i(sm);
     }
-    dft<RD, true>(y);
+    if constexpr (RD == 8) {
+      dft8_rest<true>(p, q, y);
+    } else {
+      dft4_rest<true>(p[0], q[0], p[1], q[1], y[0], y[1], y[2], y[3]);
+    }
 #pragma unroll
     for (int r = 0; r < RD; ++r) buf[spad<double2>(e0 + r)] = y[r];
   }
@@ -517,10 +552,17 @@ __device__ __forceinline__ void lf_derivative(double2* buf, int nb, const HOp<do
     L /= RD;
     __syncthreads();
   }
-  if (np - 1 < n8)
-    lf_center<8, true>(buf, n, nb, kd, ent, flg, second);
-  else
-    lf_center<4, true>(buf, n, nb, kd, ent, flg, second);
+  if (np - 1 < n8) {
+    if (second)
+      lf_center<8, true, true>(buf, n, nb, kd, ent, flg);
+    else
+      lf_center<8, true, false>(buf, n, nb, kd, ent, flg);
+  } else {
+    if (second)
+      lf_center<4, true, true>(buf, n, nb, kd, ent, flg);
+    else
+      lf_center<4, true, false>(buf, n, nb, kd, ent, flg);
+  }
   ent += (L == 8 ? 4 : 2) * (n / L);
   flg += n / L;
   __syncthreads();
@@ -592,16 +634,15 @@ __device__ __noinline__ void spectral_derivative(typename Cx<R>::T* buf, int nb,
   }
 }
 
+// Elements per thread in flight in the pointwise passes of H psi.
+constexpr int kHpsiUnroll = 1;
+
 // Coupling F_{st}(q_j) from the stored upper triangle (S(S-1)/2 rows of n).
 template <typename R>
 __device__ __forceinline__ R coupling(const R* __restrict__ F, int n, int S, int s, int t, int j) {
-  if (s < t) {
-    const int p = s * S - (s * (s + 1)) / 2 + (t - s - 1);
-    return __ldg(F + (size_t)p * n + j);
-  } else {
-    const int p = t * S - (t * (t + 1)) / 2 + (s - t - 1);
-    return -__ldg(F + (size_t)p * n + j);
-  }
+  const int a = s < t ? s : t, b = s < t ? t : s;
+  const int p = a * S - (a * (a + 1)) / 2 + (b - a - 1);
+  return neg_if(__ldg(F + (size_t)p * n + j), s > t);   // F_ts = -F_st
 }
 
 // Diabatic coupling W_st (s != t) from the stored upper triangle (symmetric).
@@ -757,40 +798,75 @@ __device__ __noinline__ void apply_h_staged(const HOp<R>& H, typename Cx<R>::T* 
   const bool whole = nb == S;
   C* sb = in_dyn_smem(sbuf);
   C* su = in_dyn_smem(sU);
-  // U = (D + F) x
+  const int tot = nb * n;
+  constexpr int U = kHpsiUnroll;
+  // (D + F) of the batch's points: the FFT result plus the coupling to the
+  // other surfaces' w (S = 2: +-F_01 w_other)
+  auto plus_fw = [&](int s, int j, C acc, const C* w) {
+    if (S == 2) return caxpy_r(neg_if(__ldg(F + j), s != 0), w[(1 - s) * n + j], acc);
+    for (int t = 0; t < S; ++t)
+      if (t != s) acc = caxpy_r(coupling(F, n, S, s, t, j), w[t * n + j], acc);
+    return acc;
+  };
+  // U = (D + F) x; U elements per thread formed before any is stored
   for (int s0 = 0; s0 < S; s0 += nb) {
     spectral_derivative<R>(sbuf, nb, H, x + (size_t)s0 * n);
-    for (int i = threadIdx.x; i < nb * n; i += kThreads) {
-      const int s = s0 + (i >> ln), j = i & (n - 1);
-      C acc = sb[spad<C>(i)];
-      for (int t = 0; t < S; ++t)
-        if (t != s) acc = caxpy_r(coupling(F, n, S, s, t, j), x[t * n + j], acc);
-      su[s * n + j] = acc;
-      if (whole) sb[spad<C>(i)] = acc;
+    for (int i0 = threadIdx.x; i0 < tot; i0 += U * kThreads) {
+      C acc[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * kThreads;
+        if (i < tot) acc[u] = plus_fw(s0 + (i >> ln), i & (n - 1), sb[spad<C>(i)], x);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * kThreads;
+        if (i < tot) {
+          su[s0 * n + i] = acc[u];
+          if (whole) sb[spad<C>(i)] = acc[u];
+        }
+      }
     }
     __syncthreads();
   }
   // y = e z + a x + c (-hbar^2/2m (D + F) U + V x); the Lanczos iteration
-  // (a = 0, c = 1) skips the scalings
+  // (a = 0, c = 1) skips the scalings.  The operands of U elements per
+  // thread are loaded before any result is stored (y may alias x or z, but
+  // element by element only).
   const R mh = -H.h2m;
   const bool plain = a == (R)0 && c.x == (R)1 && c.y == (R)0;
   R d[2] = {(R)0, (R)0};
   for (int s0 = 0; s0 < S; s0 += nb) {
     spectral_derivative<R>(sbuf, nb, H, whole ? nullptr : su + (size_t)s0 * n);
-    for (int i = threadIdx.x; i < nb * n; i += kThreads) {
-      const int s = s0 + (i >> ln), j = i & (n - 1);
-      C acc = sb[spad<C>(i)];
-      for (int t = 0; t < S; ++t)
-        if (t != s) acc = caxpy_r(coupling(F, n, S, s, t, j), su[t * n + j], acc);
-      const C xs = x[s * n + j];
-      const R v = __ldg(V + s * n + j);
-      const C hx = cmk<C>(fma(mh, acc.x, v * xs.x), fma(mh, acc.y, v * xs.y));
-      C out = plain ? hx : caxpy(c, hx, cmk<C>(a * xs.x, a * xs.y));
-      if (e != (R)0) out = caxpy_r(e, z[s * n + j], out);
-      y[s * n + j] = out;
-      if (DOTS) {
-        d[0] = fma(xs.x, out.x, fma(xs.y, out.y, d[0]));
-        d[1] = fma(out.x, out.x, fma(out.y, out.y, d[1]));
+    const C* xb = x + (size_t)s0 * n;
+    const C* zb = z + (size_t)s0 * n;
+    const R* Vb = V + (size_t)s0 * n;
+    for (int i0 = threadIdx.x; i0 < tot; i0 += U * kThreads) {
+      C acc[U], xs[U], zz[U];
+      R v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * kThreads;
+        if (i < tot) {
+          acc[u] = plus_fw(s0 + (i >> ln), i & (n - 1), sb[spad<C>(i)], su);
+          xs[u] = xb[i];
+          v[u] = __ldg(Vb + i);
+          zz[u] = e != (R)0 ? zb[i] : cmk<C>((R)0, (R)0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * kThreads;
+        if (i < tot) {
+          const C hx = cmk<C>(fma(mh, acc[u].x, v[u] * xs[u].x), fma(mh, acc[u].y, v[u] * xs[u].y));
+          C out = plain ? hx : caxpy(c, hx, cmk<C>(a * xs[u].x, a * xs[u].y));
+          if (e != (R)0) out = caxpy_r(e, zz[u], out);
+          y[s0 * n + i] = out;
+          if (DOTS) {
+            d[0] = fma(xs[u].x, out.x, fma(xs[u].y, out.y, d[0]));
+            d[1] = fma(out.x, out.x, fma(out.y, out.y, d[1]));
+          }
+        }
       }
     }
     __syncthreads();

@@ -121,6 +121,25 @@ struct Dom1D {
     const int n = len;
     for (int i = threadIdx.x; i < n; i += kThreads) f(i);
   }
+  // each with U elements per thread in flight: ld(i) returns element i's
+  // operands, st(i, t) computes and stores.  The loads of a group of U
+  // elements precede its stores, so each thread keeps U sets of loads in
+  // flight instead of one (8 warps per SM cannot hide the L2 latency with
+  // one).  ld(i) and st(i, t) must touch element i only.
+  template <int U, class Ld, class St>
+  __device__ __forceinline__ void each_u(Ld&& ld, St&& st) {
+    const int n = len;
+    using T = decltype(ld(0));
+    int i = threadIdx.x;
+    for (; i + (U - 1) * kThreads < n; i += U * kThreads) {
+      T t[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) t[u] = ld(i + u * kThreads);
+#pragma unroll
+      for (int u = 0; u < U; ++u) st(i + u * kThreads, t[u]);
+    }
+    for (; i < n; i += kThreads) st(i, ld(i));
+  }
   template <int K, typename R>
   __device__ __forceinline__ bool sum(R (&v)[K], R* out) {
     cta_sum<K>(v, reinterpret_cast<R*>(red), out);

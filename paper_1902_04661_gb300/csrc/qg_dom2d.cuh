@@ -106,6 +106,11 @@ struct Dom2D {
       for (int k = threadIdx.x; k < per; k += kThreads) f(base + k);
     }
   }
+  // each with loads and stores split (see the 1-D domain); one at a time here
+  template <int U, class Ld, class St>
+  __device__ __forceinline__ void each_u(Ld&& ld, St&& st) {
+    each([&](int i) { st(i, ld(i)); });
+  }
 
   // Adds the per-CTA partial sums buf[b * 32 + k], b < gridDim.x, k < K:
   // warp w handles k = w, w + kWarps, ..., loads 32 partials at a time and

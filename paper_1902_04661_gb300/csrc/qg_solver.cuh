@@ -87,6 +87,9 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
                               typename Cx<R>::T* X, typename Cx<R>::T* work, Counters& cnt, R* sc,
                               double* res_out);
 
+// Elements per thread in flight in the Lanczos vector passes.
+constexpr int kLanczosUnroll = 4;
+
 template <typename R>
 __device__ __forceinline__ void count_hpsi(Counters& cnt) {
   if (sizeof(R) == 8)
@@ -317,6 +320,12 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
                               typename Cx<R>::T* X, typename Cx<R>::T* work, Counters& cnt, R* sc,
                               double* res_out) {
   using C = typename Cx<R>::T;
+  struct C2 {
+    C a, b;
+  };
+  struct C5 {
+    C v, dp, dq, x, w;
+  };
   const int len = D.len;
   const R dv = (R)D.dv;
   const C mic = cmk<C>((R)0, -tau);
@@ -393,11 +402,12 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
         if (!D.ok()) return false;
         alpha = dv * sc[0];
         R wv[1] = {0};
-        D.each([&](int i) {
-          const C w = caxpy_r(-alpha, Vc[i], Wn[i]);
-          Wn[i] = w;
-          wv[0] = fma(w.x, w.x, fma(w.y, w.y, wv[0]));
-        });
+        D.template each_u<kLanczosUnroll>([&](int i) { return C2{Vc[i], Wn[i]}; },
+                                          [&](int i, const C2& t) {
+                                            const C w = caxpy_r(-alpha, t.a, t.b);
+                                            Wn[i] = w;
+                                            wv[0] = fma(w.x, w.x, fma(w.y, w.y, wv[0]));
+                                          });
         if (!D.template sum<1>(wv, sc)) return false;
         betan = sqrt(dv * sc[0]);
       } else {
@@ -461,16 +471,17 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
       const R rr = (R)1 / fma(r.x, r.x, r.y * r.y);
       const C ir = cmk<C>(r.x * rr, -r.y * rr);
       const R ibn = betan > (R)0 ? (R)1 / betan : (R)0;
-      D.each([&](int i) {
-        const C v = Vc[i];
-        C d = v;
-        d = cnaxpy(del, Dp[i], d);
-        d = cnaxpy(eps, Dq[i], d);
-        d = cmul(d, ir);
-        Dq[i] = d;                                   // newest direction, in the oldest slot
-        X[i] = caxpy(gk, d, X[i]);
-        Wn[i] = cscale(ibn, Wn[i]);                  // v_{k+1}
-      });
+      D.template each_u<kLanczosUnroll>(
+          [&](int i) { return C5{Vc[i], Dp[i], Dq[i], X[i], Wn[i]}; },
+          [&](int i, const C5& t) {
+            C d = t.v;
+            d = cnaxpy(del, t.dp, d);
+            d = cnaxpy(eps, t.dq, d);
+            d = cmul(d, ir);
+            Dq[i] = d;                               // newest direction, in the oldest slot
+            X[i] = caxpy(gk, d, t.x);
+            Wn[i] = cscale(ibn, t.w);                // v_{k+1}
+          });
       __syncthreads();
       C* t0 = Dq;
       Dq = Dp;
