@@ -346,6 +346,8 @@ Inst2D make_inst2d(const qg_state* s) {
     I.dv *= g->dq[d];
     I.tw[d] = g->d_tw[d];
     I.kd[d] = g->d_kd[d];
+    I.lf[d] = g->d_lf[d];
+    I.lff[d] = g->d_lff[d];
     I.tw32[d] = g->d_tw32[d];
     I.kd32[d] = g->d_kd32[d];
   }

@@ -281,12 +281,9 @@ struct DomC {
   }
 
   __device__ __forceinline__ double coup(int s, int t, int j) const {
-    if (s < t) {
-      const int p = s * S - (s * (s + 1)) / 2 + (t - s - 1);
-      return F[p * M + j];
-    }
-    const int p = t * S - (t * (t + 1)) / 2 + (s - t - 1);
-    return -F[p * M + j];
+    const int a = s < t ? s : t, b = s < t ? t : s;
+    const int p = a * S - (a * (a + 1)) / 2 + (b - a - 1);
+    return neg_if(F[p * M + j], s > t);   // F_ts = -F_st
   }
 
   // y = e z + a x + c (H x), H = -hbar^2/2m (D + F)^2 + V (Eq. adiab_mol_ham

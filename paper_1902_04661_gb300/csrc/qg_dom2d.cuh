@@ -310,21 +310,19 @@ struct Dom2D {
   // F_{st} at flattened point p from one dimension's upper triangle.
   template <typename R>
   __device__ static __forceinline__ R coupling2(const R* Fd, int N, int S, int s, int t, size_t p) {
-    if (s < t) {
-      const int q = s * S - (s * (s + 1)) / 2 + (t - s - 1);
-      return __ldg(Fd + (size_t)q * N + p);
-    }
-    const int q = t * S - (t * (t + 1)) / 2 + (s - t - 1);
-    return -__ldg(Fd + (size_t)q * N + p);
+    const int a = s < t ? s : t, b = s < t ? t : s;
+    const int q = a * S - (a * (a + 1)) / 2 + (b - a - 1);
+    return neg_if(__ldg(Fd + (size_t)q * N + p), s > t);   // F_ts = -F_st
   }
 };
 
 // Shared-memory copy of both dimensions' FFT tables: FP64 twiddles, FP64
 // wave numbers, FP32 twiddles, FP32 wave numbers, each dimension 0 then 1
-// (36 (n0 + n1) bytes).  The 2-D units read global memory through L2 only,
-// so tables kept in global memory would cost an L2 round trip every pass.
+// (36 (n0 + n1) bytes), then the FP64 Linzer-Feig factor tables of
+// dimension 0 and 1.  The 2-D units read global memory through L2 only, so
+// tables kept in global memory would cost an L2 round trip every pass.
 __host__ __device__ inline size_t tables2d_bytes(int n0, int n1) {
-  return ((size_t)36 * (n0 + n1) + 15) / 16 * 16;
+  return ((size_t)36 * (n0 + n1) + 15) / 16 * 16 + lf_table_bytes(n0) + lf_table_bytes(n1);
 }
 
 // tab_off > 0: the tables are copied to dyn + tab_off (16-byte aligned) and
@@ -359,6 +357,8 @@ static __device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_
     D.H64[d].h2m = I.h2m[d];
     D.H64[d].tw = I.tw[d];
     D.H64[d].kd = I.kd[d];
+    D.H64[d].lf = I.lf[d];
+    D.H64[d].lff = I.lff[d];
     D.H32[d].n = I.n[d];
     D.H32[d].S = I.S;
     D.H32[d].npass = I.npass[d];
@@ -388,6 +388,19 @@ static __device__ Dom2D make_dom2d(const Inst2D& I, unsigned char* dyn, int fft_
       D.H32[d].tw = tw32 + base;
       D.H32[d].kd = kd32 + base;
       base += n;
+    }
+    // then the factor tables of both dimensions (whole 16-byte words each)
+    unsigned char* lft = t + (((size_t)36 * nt + 15) / 16 * 16);
+    for (int d = 0; d < 2; ++d) {
+      if (!I.lf[d]) continue;
+      const int words = (int)(lf_table_bytes(I.n[d]) / 16);
+      const int4* src = reinterpret_cast<const int4*>(I.lf[d]);
+      int4* dst = reinterpret_cast<int4*>(lft);
+      for (int k = threadIdx.x; k < words; k += kThreads) dst[k] = src[k];
+      D.H64[d].lf = reinterpret_cast<const double2*>(lft);
+      D.H64[d].lff = reinterpret_cast<const unsigned*>(
+          lft + (reinterpret_cast<const unsigned char*>(I.lff[d]) - reinterpret_cast<const unsigned char*>(I.lf[d])));
+      lft += (size_t)words * 16;
     }
     __syncthreads();
   }

@@ -182,6 +182,8 @@ struct Inst2D {
   double dv;
   const double2* tw[2];
   const double* kd[2];
+  const double2* lf[2];     // Linzer-Feig factor tables of each dimension's FP64 transform, or null
+  const unsigned* lff[2];
   const float2* tw32[2];
   const float* kd32[2];
   const double* V;     // S * N
