@@ -68,22 +68,6 @@ void freq_positions(int len, const int* radix, int npass, std::vector<int>& f) {
     for (int pp = 0; pp < m; ++pp) f[q * m + pp] = q + R * sub[pp];
 }
 
-// Accumulated frequency K of block blk of a forward pass preceded by the
-// passes radix[0..] that made nbk blocks: the block index read as
-// mixed-radix digits (first pass most significant), digits reversed.
-int block_frequency(int blk, const int* radix, int nbk) {
-  int K = 0, mult = 1, rem = blk, size = nbk, i = 0;
-  while (size > 1) {
-    const int R = radix[i++];
-    size /= R;
-    const int d = rem / size;
-    rem -= d * size;
-    K += d * mult;
-    mult *= R;
-  }
-  return K;
-}
-
 // w = exp(sgn 2 pi i num / den) in Linzer and Feig's factored form: w = s (1
 // + i t) (form 0, |Re w| >= |Im w|) or w = s (t + i) (form 1), so |t| <= 1.
 // cos and sin are evaluated in long double on at most an eighth of a turn

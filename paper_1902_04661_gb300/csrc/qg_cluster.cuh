@@ -113,6 +113,27 @@ __device__ __forceinline__ void fft_last_cross(double2* gbuf, int M, int nb, con
   }
 }
 
+// The same last forward pass in the factored form of the one-CTA transform
+// (set blk of the pass's factor tables), then the cross twiddle.
+template <int RD>
+__device__ __forceinline__ void lf_last_cross(double2* gbuf, int M, int nb, const double2* __restrict__ ent,
+                                              const unsigned* __restrict__ flg, const double2* __restrict__ cw) {
+  double2* buf = in_dyn_smem(gbuf);
+  const int total = (nb * M) / RD;
+  for (int b = threadIdx.x; b < total; b += kThreads) {
+    const int e0 = b * RD;
+    const int pos = e0 & (M - 1);
+    double2 x[RD];
+#pragma unroll
+    for (int r = 0; r < RD; ++r) x[r] = buf[spad<double2>(e0 + r)];
+    LfW w[RD == 8 ? 4 : 2];
+    lf_load<RD>(ent, flg, M / RD, pos / RD, w);
+    lf_bfly<RD, false>(x, w);
+#pragma unroll
+    for (int k = 0; k < RD; ++k) buf[spad<double2>(e0 + k)] = cmul(x[bitrev<RD>(k)], cw[pos + k]);
+  }
+}
+
 // Conjugate cross twiddle, then the first inverse pass (block length RD).
 template <int RD>
 __device__ __forceinline__ void fft_first_cross_inv(double2* gbuf, int M, int nb, const double2* __restrict__ cw) {
@@ -173,7 +194,8 @@ struct DomC {
   const double* F;      // S(S-1)/2 x M
   double2* U;
   double2* fb;          // padded FFT buffer, S x M
-  const double2* twl;   // local twiddles, pass by pass
+  const double2* lf;    // factor tables of the local transform (see lf_tables)
+  const unsigned* lff;
   const double2* cw;    // cross twiddles w_N^{r k2(p)}
   const double* kc;     // centre wave numbers / N: Q x G
   double2* basis64;
@@ -212,27 +234,46 @@ struct DomC {
 
   __device__ __forceinline__ bool ok() const { return true; }
 
-  // buf <- D buf (all S local vectors), see the file comment.
+  // buf <- D buf (all S local vectors), see the file comment.  The local
+  // passes are those of the one-CTA FP64 transform (lf_pass): the first
+  // forward pass untwiddled, the others factored.
   __device__ __noinline__ void derivative(double2* buf) {
     const int np = lp.npass, n8 = lp.n8;
-    int L = M, off = 0;
+    const double2* ent = lf;
+    const unsigned* flg = lff;
+    int L = M;
     for (int i = 0; i < np - 1; ++i) {
-      if (i < n8) {
-        fft_pass<8, false>(buf, M, S, L, twl + off);
-        off += 7 * (L / 8);
-        L /= 8;
+      const int RD = i < n8 ? 8 : 4;
+      if (i == 0) {
+        if (RD == 8)
+          lf_pass<8, false, false>(buf, M, S, L, nullptr, nullptr);
+        else
+          lf_pass<4, false, false>(buf, M, S, L, nullptr, nullptr);
       } else {
-        fft_pass<4, false>(buf, M, S, L, twl + off);
-        off += 3 * (L / 4);
-        L /= 4;
+        if (RD == 8)
+          lf_pass<8, false, true>(buf, M, S, L, ent, flg);
+        else
+          lf_pass<4, false, true>(buf, M, S, L, ent, flg);
+        ent += (RD == 8 ? 4 : 2) * (M / L);
+        flg += M / L;
       }
+      L /= RD;
       __syncthreads();
     }
     const bool last8 = np - 1 < n8;
-    if (last8)
-      fft_last_cross<8>(buf, M, S, cw);
-    else
-      fft_last_cross<4>(buf, M, S, cw);
+    if (np == 1) {
+      if (last8)
+        fft_last_cross<8>(buf, M, S, cw);
+      else
+        fft_last_cross<4>(buf, M, S, cw);
+    } else {
+      if (last8)
+        lf_last_cross<8>(buf, M, S, ent, flg, cw);
+      else
+        lf_last_cross<4>(buf, M, S, ent, flg, cw);
+      ent += (L == 8 ? 4 : 2) * (M / L);
+      flg += M / L;
+    }
     if constexpr (G > 1)
       cluster_barrier();
     else
@@ -271,11 +312,12 @@ struct DomC {
     for (int i = np - 2; i >= 0; --i) {
       const int RD = i < n8 ? 8 : 4;
       L *= RD;
-      off -= (RD - 1) * (L / RD);
       if (RD == 8)
-        fft_pass<8, true>(buf, M, S, L, twl + off);
+        lf_pass<8, true, true>(buf, M, S, L, ent, flg);
       else
-        fft_pass<4, true>(buf, M, S, L, twl + off);
+        lf_pass<4, true, true>(buf, M, S, L, ent, flg);
+      ent += (RD == 8 ? 4 : 2) * (L / RD);
+      flg += L / RD;
       __syncthreads();
     }
   }
@@ -326,7 +368,7 @@ struct DomC {
 
 // Dynamic shared memory of the cluster form for one instance shape.
 struct ClusterSmem {
-  size_t fb, vec, lanczos, V, F, twl, cw, kc, k2, part, total;
+  size_t fb, vec, lanczos, V, F, lf, cw, kc, k2, part, total;
 };
 
 __host__ __device__ inline ClusterSmem cluster_smem_layout(int M, int S, int G, int restart) {
@@ -346,8 +388,8 @@ __host__ __device__ inline ClusterSmem cluster_smem_layout(int M, int S, int G, 
   off += ((size_t)S * M * 8 + 255) & ~size_t(255);
   L.F = off;
   off += ((size_t)(S * (S - 1) / 2) * M * 8 + 255) & ~size_t(255);
-  L.twl = off;
-  off += (size_t)M * 16;
+  L.lf = off;
+  off += (lf_table_bytes(M) + 255) & ~size_t(255);
   L.cw = off;
   off += (size_t)M * 16;
   L.kc = off;
@@ -361,30 +403,81 @@ __host__ __device__ inline ClusterSmem cluster_smem_layout(int M, int S, int G, 
   return L;
 }
 
-// Tables of the local plan: twiddles pass by pass (for forward pass i with
-// block length L, radix R, m = L / R, entry (r - 1) m + j holds
-// exp(-2 pi i j r / L)), the frequency k2(p) held at each position p after
-// the forward passes, the cross twiddles w_N^{rank k2(p)} and the centre wave
-// numbers k(k2 + M k1) / N of this CTA's centre positions.
-template <int G>
-__device__ void build_cluster_tables(const LocalPlan& lp, int n, double dq, int rank, int q0, int Q, double2* twl,
-                                     double2* cw, double* kc, int* k2tab) {
-  const int M = lp.M;
-  for (int k = threadIdx.x; k < M; k += kThreads) {
-    int L = M, off = 0, e = 0;
-    for (int i = 0; i < lp.npass - 1; ++i) {
-      const int R = lp.radix[i], m = L / R, seg = (R - 1) * m;
-      if (k < off + seg) {
-        const int r = (k - off) / m + 1, j = (k - off) - (r - 1) * m;
-        e = j * r * (M / L);
-        break;
+// w = exp(sgn 2 pi i num / den) in the factored form s (1 + i t) (form 0,
+// |Re w| >= |Im w|) or s (t + i) (form 1); 2 num / den is a dyadic fraction,
+// exact in a double, for sincospi.
+__device__ __forceinline__ void lf_factor_dev(long long num, long long den, int sgn, double2* st, unsigned* form) {
+  num %= den;
+  if (num < 0) num += den;
+  double s, c;
+  sincospi(2.0 * (double)num / (double)den, &s, &c);
+  if (sgn < 0) s = -s;
+  if (fabs(c) >= fabs(s)) {
+    *st = make_double2(c, s / c);
+    *form = 0u;
+  } else {
+    *st = make_double2(s, c / s);
+    *form = 1u;
+  }
+}
+
+// Factor tables of the local transform, in the layout of the one-CTA
+// transform's tables (forward passes 1..np-1 one set per block, then inverse
+// passes np-2..0 one set per position; entry e of set k at e * nsets + k;
+// one word of form bits per set).  ent must hold lf_table_bytes(M).
+static __device__ void build_local_lf(const LocalPlan& lp, double2* ent, unsigned* flg) {
+  const int M = lp.M, np = lp.npass;
+  int Ls[QG_MAX_PASSES];
+  for (int i = 0, L = M; i < np; ++i) {
+    Ls[i] = L;
+    L /= lp.radix[i];
+  }
+  for (int i = 1; i < np; ++i) {
+    const int R = lp.radix[i], E = R == 8 ? 4 : 2, o = R == 8 ? 0 : 1, nbk = M / Ls[i];   // radix 4: W^2, W
+    const long long B = (long long)nbk * R;
+    for (int k = threadIdx.x; k < nbk; k += kThreads) {
+      const long long K = block_frequency(k, lp.radix, nbk);
+      const long long a[4] = {4 * K, 2 * K, K, 8 * K + B}, b[4] = {B, B, B, 8 * B};
+      unsigned fl = 0u;
+      for (int e = 0; e < E; ++e) {
+        unsigned f = 0u;
+        lf_factor_dev(a[e + o], b[e + o], -1, &ent[(size_t)e * nbk + k], &f);
+        fl |= f << e;
       }
-      off += seg;
-      L /= R;
+      flg[k] = fl;
     }
+    ent += (size_t)E * nbk;
+    flg += nbk;
+  }
+  for (int i = np - 2; i >= 0; --i) {
+    const int R = lp.radix[i], E = R == 8 ? 4 : 2, o = R == 8 ? 0 : 1, m = Ls[i] / R;
+    const long long Lb = Ls[i];
+    for (int j = threadIdx.x; j < m; j += kThreads) {
+      const long long a[4] = {4LL * j, 2LL * j, (long long)j, 8LL * j + Lb}, b[4] = {Lb, Lb, Lb, 8 * Lb};
+      unsigned fl = 0u;
+      for (int e = 0; e < E; ++e) {
+        unsigned f = 0u;
+        lf_factor_dev(a[e + o], b[e + o], +1, &ent[(size_t)e * m + j], &f);
+        fl |= f << e;
+      }
+      flg[j] = fl;
+    }
+    ent += (size_t)E * m;
+    flg += m;
+  }
+}
+
+// Tables of the local plan: the factor tables (build_local_lf), the
+// frequency k2(p) held at each position p after the forward passes, the
+// cross twiddles w_N^{rank k2(p)} and the centre wave numbers k(k2 + M k1) / N
+// of this CTA's centre positions.
+template <int G>
+__device__ void build_cluster_tables(const LocalPlan& lp, int n, double dq, int rank, int q0, int Q, double2* lfe,
+                                     unsigned* lff, double2* cw, double* kc, int* k2tab) {
+  const int M = lp.M;
+  build_local_lf(lp, lfe, lff);
+  for (int k = threadIdx.x; k < M; k += kThreads) {
     double s, c;
-    sincospi(2.0 * (double)e / (double)M, &s, &c);
-    twl[k] = make_double2(c, -s);
     int f = 0, mult = 1, rem = k, len = M;
     for (int i = 0; i < lp.npass; ++i) {
       const int m = len / lp.radix[i];
@@ -441,7 +534,12 @@ __device__ void run_cluster_instance(const InstDesc& I, const StepPlan& P, unsig
   double2* psi = vec + len;
   double2* B = vec + 2 * len;
   double2* X = vec + 3 * len;
-  D.twl = reinterpret_cast<const double2*>(dyn + L.twl);
+  int lf_entries = 0, lf_sets = 0;
+  lf_counts(D.lp.radix, D.lp.npass, M, &lf_entries, &lf_sets);
+  double2* lfe = reinterpret_cast<double2*>(dyn + L.lf);
+  unsigned* lff = reinterpret_cast<unsigned*>(lfe + lf_entries);
+  D.lf = lfe;
+  D.lff = lff;
   D.cw = reinterpret_cast<const double2*>(dyn + L.cw);
   D.kc = reinterpret_cast<const double*>(dyn + L.kc);
   const size_t SN = (size_t)S * n;
@@ -455,9 +553,8 @@ __device__ void run_cluster_instance(const InstDesc& I, const StepPlan& P, unsig
   D.res64 = nullptr;
   D.r32 = D.d32 = D.basis32 = nullptr;
   double2* P0 = I.work + 3 * SN + (size_t)rank * len;
-  build_cluster_tables<G>(D.lp, n, I.dq, rank, D.q0, D.Q, reinterpret_cast<double2*>(dyn + L.twl),
-                          reinterpret_cast<double2*>(dyn + L.cw), reinterpret_cast<double*>(dyn + L.kc),
-                          reinterpret_cast<int*>(dyn + L.k2));
+  build_cluster_tables<G>(D.lp, n, I.dq, rank, D.q0, D.Q, lfe, lff, reinterpret_cast<double2*>(dyn + L.cw),
+                          reinterpret_cast<double*>(dyn + L.kc), reinterpret_cast<int*>(dyn + L.k2));
   // this CTA's points j = rank + G n2 of the fields and of psi
   for (int i = threadIdx.x; i < len; i += kThreads) {
     const int s = i / M, n2 = i - s * M;

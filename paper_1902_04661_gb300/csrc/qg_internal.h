@@ -50,6 +50,22 @@ __host__ __device__ inline FftPlan make_plan(int n) {
   return p;
 }
 
+// Accumulated frequency K of block blk of a forward pass preceded by the
+// passes radix[0..] that made nbk blocks: the block index read as
+// mixed-radix digits (first pass most significant), digits reversed.
+__host__ __device__ inline int block_frequency(int blk, const int* radix, int nbk) {
+  int K = 0, mult = 1, rem = blk, size = nbk, i = 0;
+  while (size > 1) {
+    const int R = radix[i++];
+    size /= R;
+    const int d = rem / size;
+    rem -= d * size;
+    K += d * mult;
+    mult *= R;
+  }
+  return K;
+}
+
 // Sizes of the Linzer-Feig factor tables of the FP64 transform of a plan
 // (qg_api.cu, lf_tables): one set of factors per block of forward passes
 // 1..npass-1 and per position of inverse passes 0..npass-2, 4 double2
