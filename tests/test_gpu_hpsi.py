@@ -11,7 +11,7 @@ from oracle import fields as ofields, grid as ogrid, hamiltonian as oham, initia
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,S", [(8, 2), (16, 3), (32, 4), (64, 2), (256, 3), (512, 2), (1024, 2), (1024, 4)])
+@pytest.mark.parametrize("n,S", [(8, 2), (16, 3), (32, 4), (64, 2), (128, 2), (256, 3), (512, 2), (1024, 2), (1024, 4)])
 def test_hpsi_random_fields_vs_dense_oracle(qglib, cuda, n, S):
     qmin, qmax, mass = -2.0, 9.0, 13.0
     V, F = wl.random_adiabatic_fields(S, 1, (n,), seed=100 + n + S)
@@ -38,19 +38,34 @@ def test_hpsi_nai_like_full_size_vs_matrix_free_oracle(qglib, cuda, n):
     assert rel_l2(got, want) < 1e-12
 
 
-def test_hpsi_plane_waves_free_particle(qglib, cuda):
-    n, qmin, qmax, mass = 128, 0.0, 10.0, 3.0
+@pytest.mark.parametrize("n", [8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192])
+def test_hpsi_plane_waves_free_particle(qglib, cuda, n):
+    """Every transform plan (radix-8 and radix-4 passes, the factored FP64
+    passes from N = 16 on): on a grid plane wave e^{ikq} with V = F = 0, H psi
+    = k^2 / 2m psi exactly, the Nyquist wave included.  The bound is the
+    rounding of a length-n transform, log2(n) eps times the largest k^2 / 2m."""
+    qmin, mass = 0.0, 3.0
+    qmax = 0.05 * n
     g = qglib.Grid([n], [qmin], [qmax])
     m = qglib.Model(g, 2, [mass], V=np.zeros((2, n)), F=np.zeros((1, 1, n)))
     st = qglib.State(m)
-    q, dq = ogrid.points(qmin, qmax, n)
     k = ogrid.wavenumbers(qmin, qmax, n)
-    for j in (0, 1, 5, n // 2 - 1, n // 2, n - 1):
-        psi = np.stack([np.exp(1j * k[j] * q), np.exp(1j * k[(j + 3) % n] * q)])
+    emax = np.max(k ** 2) / (2 * mass)
+    tol = 1e-13 + 2e-14 * np.log2(n) * emax
+    p = np.arange(n)
+
+    def wave(j):
+        # e^{i k_j q_p} = e^{2 pi i j p / n} (qmin = 0), the phase reduced
+        # exactly in integers: exp of k q itself would carry the rounding of
+        # k q (up to ~3000 rad here), which the k^2 multiplier amplifies
+        return np.exp(2j * np.pi * ((j * p) % n) / n)
+
+    for j in sorted({0, 1, 5 % n, n // 2 - 1, n // 2, n - 1}):
+        psi = np.stack([wave(j), wave((j + 3) % n)])
         st.set(psi)
         got = st.apply_h()
         want = np.stack([k[j] ** 2 / (2 * mass) * psi[0], k[(j + 3) % n] ** 2 / (2 * mass) * psi[1]])
-        assert np.abs(got - want).max() < 1e-12 * max(1.0, np.abs(want).max())
+        assert np.abs(got - want).max() < tol, (n, j, np.abs(got - want).max(), tol)
 
 
 def test_model_fields_from_diabatic_vs_oracle(qglib, cuda):
