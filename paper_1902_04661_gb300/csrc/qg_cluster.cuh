@@ -151,30 +151,45 @@ __device__ __forceinline__ void fft_first_cross_inv(double2* gbuf, int M, int nb
   }
 }
 
-// Radix plan of the local length M (as for the full grids: radix-8 passes,
-// then one or two radix-4 passes).
+// Radix plan of the local length M.  As for the full grids (radix-8 passes,
+// then one or two radix-4 passes) while a radix-8 pass still gives four warps
+// a butterfly each (S M / 8 >= 128); below that, radix-4 passes (one radix-8
+// pass first when log2 M is odd), which occupy twice as many threads per pass
+// for the same FP64 work per point -- the FP64 units of an SM sit in its four
+// schedulers, and a pass of 64 radix-8 butterflies keeps only two of them
+// busy.
 struct LocalPlan {
   int M, npass, n8;
   int radix[QG_MAX_PASSES];
 };
 
-__device__ __forceinline__ LocalPlan local_plan(int M) {
+__host__ __device__ inline LocalPlan local_plan(int M, int S) {
   LocalPlan p;
   p.M = M;
-  const int k = ilog2(M);
-  int a = k / 3;
-  const int rem = k % 3;
-  if (rem == 1) a -= 1;
+  int k = 0;
+  while ((1 << k) < M) ++k;
   p.npass = 0;
-  for (int i = 0; i < a; ++i) p.radix[p.npass++] = 8;
-  if (rem == 2) p.radix[p.npass++] = 4;
-  if (rem == 1) {
-    p.radix[p.npass++] = 4;
-    p.radix[p.npass++] = 4;
+  if ((S * M) / 8 >= 4 * 32) {
+    const FftPlan f = make_plan(M);
+    for (int i = 0; i < f.npass; ++i) p.radix[p.npass++] = f.radix[i];
+  } else {
+    if (k % 2 == 1) {
+      p.radix[p.npass++] = 8;
+      k -= 3;
+    }
+    for (; k > 0; k -= 2) p.radix[p.npass++] = 4;
   }
   for (int i = p.npass; i < QG_MAX_PASSES; ++i) p.radix[i] = 1;
   p.n8 = count_radix8(p.radix, p.npass);
   return p;
+}
+
+// Bytes of the local plan's factor tables (entries, then form words).
+__host__ __device__ inline size_t local_lf_bytes(int M, int S) {
+  const LocalPlan p = local_plan(M, S);
+  int e = 0, st = 0;
+  lf_counts(p.radix, p.npass, M, &e, &st);
+  return ((size_t)e * 16 + (size_t)st * 4 + 15) & ~(size_t)15;
 }
 
 // The instance's share of one cluster: shared-memory vectors and tables.
@@ -389,7 +404,7 @@ __host__ __device__ inline ClusterSmem cluster_smem_layout(int M, int S, int G, 
   L.F = off;
   off += ((size_t)(S * (S - 1) / 2) * M * 8 + 255) & ~size_t(255);
   L.lf = off;
-  off += (lf_table_bytes(M) + 255) & ~size_t(255);
+  off += (local_lf_bytes(M, S) + 255) & ~size_t(255);
   L.cw = off;
   off += (size_t)M * 16;
   L.kc = off;
@@ -424,7 +439,7 @@ __device__ __forceinline__ void lf_factor_dev(long long num, long long den, int 
 // Factor tables of the local transform, in the layout of the one-CTA
 // transform's tables (forward passes 1..np-1 one set per block, then inverse
 // passes np-2..0 one set per position; entry e of set k at e * nsets + k;
-// one word of form bits per set).  ent must hold lf_table_bytes(M).
+// one word of form bits per set).  ent must hold local_lf_bytes(M, S).
 static __device__ void build_local_lf(const LocalPlan& lp, double2* ent, unsigned* flg) {
   const int M = lp.M, np = lp.npass;
   int Ls[QG_MAX_PASSES];
@@ -522,7 +537,7 @@ __device__ void run_cluster_instance(const InstDesc& I, const StepPlan& P, unsig
   D.rank = rank;
   D.Q = len / G;
   D.q0 = rank * D.Q;
-  D.lp = local_plan(M);
+  D.lp = local_plan(M, S);
   D.h2m = I.h2m;
   double* Vl = reinterpret_cast<double*>(dyn + L.V);
   double* Fl = reinterpret_cast<double*>(dyn + L.F);
