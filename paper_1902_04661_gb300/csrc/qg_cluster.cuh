@@ -196,6 +196,8 @@ __host__ __device__ inline size_t local_lf_bytes(int M, int S) {
 template <int G>
 struct DomC {
   static constexpr bool kFusedDots = false;
+  // the FP64 Lanczos solve keeps its vectors in the workspace basis (lanczos_stored_solve)
+  static constexpr bool kStoredLanczos = false;
   int len;        // S M local values per vector
   double dv;
   unsigned char* gm;

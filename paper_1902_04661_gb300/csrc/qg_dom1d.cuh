@@ -98,6 +98,8 @@ struct Dom1D {
   // with U staged in shared memory, H psi forms Re<x, y> and ||y||^2 in its
   // last pass (hpsi with dots); without it the solvers reduce them separately
   static constexpr bool kFusedDots = true;
+  // the FP64 Lanczos solve keeps its vectors in the workspace basis (lanczos_stored_solve)
+  static constexpr bool kStoredLanczos = true;
   int len;
   double2* su;    // staged U (shared memory) or null
   double dv;

@@ -525,6 +525,179 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
   return false;
 }
 
+// The same minimal-residual iteration with the Lanczos vectors kept: V_0..V_k
+// in basis (m + 1 slots, the GMRES basis of the workspace).  Instead of
+// updating two search directions and X in every iteration, X += V_k y once per
+// cycle, y solving R y = g with R the banded upper-triangular factor of
+// [I; 0] + i tau T_k that the Givens rotations build (diagonal r, then del and
+// eps one and two rows above it) and g the rotated right-hand side -- in
+// exact arithmetic the iterate of lanczos_solve, X_0 + V_k R^{-1} g.  Each
+// iteration then makes one vector pass besides H psi and its normalisation.
+// Needs a domain whose H psi forms the dots (kFusedDots) and m >= 2.
+template <class Dom>
+__device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, double tau, const double2* b, double2* X,
+                                     double2* basis, Counters& cnt, double* sc, double* res_out) {
+  using C = double2;
+  const GSmem<double> sm = gsmem<double>(D.gm, P.m);
+  const int m = P.m;
+  C* rr = sm.hess;            // R_jj
+  C* rd = sm.hess + m;        // R_{j-1,j}
+  C* re = sm.hess + 2 * m;    // R_{j-2,j}
+  C* gv = sm.g;               // rotated right-hand side
+  C* yv = sm.y;
+  const int len = D.len;
+  const double dv = D.dv;
+  const C mic = make_double2(0.0, -tau);
+  double nv[1] = {0.0};
+  D.each([&](int i) {
+    const C a = b[i];
+    nv[0] = fma(a.x, a.x, fma(a.y, a.y, nv[0]));
+  });
+  if (!D.template sum<1>(nv, sc)) return false;
+  const double bn = sqrt(dv * sc[0]);
+  const double target = P.tol * bn;
+  int total = 0;
+  for (int guard = 0; guard < P.max_iters + 2; ++guard) {
+    // V_0 = r / ||r||, r = b - A X  (= b on the first cycle when X starts at zero)
+    C* V0 = basis;
+    double beta1;
+    if (guard == 0 && P.x0_zero) {
+      D.each([&](int i) { V0[i] = b[i]; });
+      __syncthreads();
+      beta1 = bn;
+    } else {
+      D.template hpsi<double>(X, V0, b, 1.0, -1.0, mic, sc);
+      count_hpsi<double>(cnt);
+      if (!D.ok()) return false;
+      beta1 = sqrt(dv * sc[1]);
+    }
+    if (guard > 0) cnt.restart++;
+    if (beta1 <= target || bn == 0.0) {
+      *res_out = (bn > 0.0) ? beta1 / bn : 0.0;
+      if (total > cnt.max_krylov) cnt.max_krylov = total;
+      return true;
+    }
+    if (total >= P.max_iters) break;
+    const double ib = 1.0 / beta1;
+    D.each([&](int i) { V0[i] = cscale(ib, V0[i]); });
+    __syncthreads();
+    C g = make_double2(beta1, 0.0);
+    double c1 = 1.0, c2 = 1.0;
+    C s1 = make_double2(0.0, 0.0), s2 = make_double2(0.0, 0.0);
+    double betak = 0.0, res_est = beta1;
+    bool conv = false;
+    int nk = 0;   // columns of this cycle
+    for (int k = 1; k <= m && total < P.max_iters; ++k) {
+      const C* Vc = basis + (size_t)(k - 1) * len;
+      C* Wn = basis + (size_t)k * len;
+      // Wn = H Vc - beta_k V_{k-2}; alpha reduced inside H psi
+      if (k == 1)
+        D.template hpsi<double>(Vc, Wn, nullptr, 0.0, 0.0, make_double2(1.0, 0.0), sc);
+      else
+        D.template hpsi<double>(Vc, Wn, basis + (size_t)(k - 2) * len, -betak, 0.0, make_double2(1.0, 0.0), sc);
+      count_hpsi<double>(cnt);
+      if (!D.ok()) return false;
+      const double alpha = dv * sc[0];
+      double wv[1] = {0.0};
+      D.each([&](int i) {
+        const C w = caxpy_r(-alpha, Vc[i], Wn[i]);
+        Wn[i] = w;
+        wv[0] = fma(w.x, w.x, fma(w.y, w.y, wv[0]));
+      });
+      if (!D.template sum<1>(wv, sc)) return false;
+      const double betan = sqrt(dv * sc[0]);
+      // column k of [I; 0] + i tau T: rows k-1, k, k+1, rotated (as lanczos_solve)
+      C eps = make_double2(0.0, 0.0);
+      C del = make_double2(0.0, tau * betak);
+      C gam = make_double2(1.0, tau * alpha);
+      const C nu = make_double2(0.0, tau * betan);
+      if (k >= 3) {
+        eps = cmul(s2, del);
+        del = cscale(c2, del);
+      }
+      if (k >= 2) {
+        const C t = caxpy(s1, gam, cscale(c1, del));
+        gam = cnaxpy(make_double2(s1.x, -s1.y), del, cscale(c1, gam));
+        del = t;
+      }
+      const double aa = hypot(gam.x, gam.y);
+      const double nn = hypot(nu.x, nu.y);
+      double c;
+      C s, r;
+      if (nn == 0.0) {
+        c = 1.0;
+        s = make_double2(0.0, 0.0);
+        r = gam;
+      } else if (aa == 0.0) {
+        c = 0.0;
+        s = make_double2(nu.x / nn, -nu.y / nn);
+        r = make_double2(nn, 0.0);
+      } else {
+        const double rho = hypot(aa, nn);
+        const C ph = make_double2(gam.x / aa, gam.y / aa);
+        c = aa / rho;
+        s = cscale(1.0 / rho, cmul(ph, make_double2(nu.x, -nu.y)));
+        r = cscale(rho, ph);
+      }
+      if (threadIdx.x == 0) {
+        rr[k - 1] = r;
+        rd[k - 1] = del;
+        re[k - 1] = eps;
+        gv[k - 1] = cscale(c, g);
+      }
+      g = make_double2(-(s.x * g.x + s.y * g.y), -(s.x * g.y - s.y * g.x));   // -conj(s) g
+      res_est = hypot(g.x, g.y);
+      nk = k;
+      total++;
+      cnt.krylov++;
+      cnt.ortho += 1;
+      cnt.update += 1;
+      c2 = c1;
+      s2 = s1;
+      c1 = c;
+      s1 = s;
+      betak = betan;
+      if (res_est <= target) {
+        conv = true;
+        break;
+      }
+      if (betan <= 1e-300) break;
+      // V_k = Wn / beta_{k+1}, needed only by further iterations
+      const double ibn = 1.0 / betan;
+      D.each([&](int i) { Wn[i] = cscale(ibn, Wn[i]); });
+      __syncthreads();
+    }
+    // y = R^{-1} g by back substitution, then X += V y
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int j = nk - 1; j >= 0; --j) {
+        C t = gv[j];
+        if (j + 1 < nk) t = cnaxpy(rd[j + 1], yv[j + 1], t);
+        if (j + 2 < nk) t = cnaxpy(re[j + 2], yv[j + 2], t);
+        const C q = rr[j];
+        const double iq = 1.0 / fma(q.x, q.x, q.y * q.y);
+        yv[j] = cmul(t, make_double2(q.x * iq, -q.y * iq));
+      }
+    }
+    __syncthreads();
+    D.each([&](int i) {
+      C x = X[i];
+      for (int j = 0; j < nk; ++j) x = caxpy(yv[j], basis[(size_t)j * len + i], x);
+      X[i] = x;
+    });
+    __syncthreads();
+    if (conv && !P.true_res) {
+      *res_out = (bn > 0.0) ? res_est / bn : 0.0;
+      if (total > cnt.max_krylov) cnt.max_krylov = total;
+      return true;
+    }
+    if (total >= P.max_iters && !conv) break;
+  }
+  if (total > cnt.max_krylov) cnt.max_krylov = total;
+  *res_out = 1e300;
+  return false;
+}
+
 template <class Dom, typename C>
 __device__ __forceinline__ void dcopy(Dom& D, C* dst, const C* src) {
   D.each([&](int i) { dst[i] = src[i]; });
@@ -537,8 +710,20 @@ __device__ bool solve_fp64(Dom& D, const StepPlan& P, double tau, const double2*
                            double* sc, int x0_zero = 0) {
   SolveParams sp{P.tol, P.restart, P.max_iters, P.reorth, P.true_res, P.solver, x0_zero};
   double res = 0.0;
-  const bool ok = P.solver == QG_SOLVER_LANCZOS ? lanczos_solve<double>(D, sp, tau, b, X, D.basis64, cnt, sc, &res)
-                                                : gmres_solve<double>(D, sp, tau, b, X, D.basis64, cnt, sc, &res);
+  bool ok;
+  if (P.solver == QG_SOLVER_LANCZOS) {
+    ok = false;
+    if constexpr (Dom::kStoredLanczos) {
+      if (sp.m >= 2)
+        ok = lanczos_stored_solve(D, sp, tau, b, X, D.basis64, cnt, sc, &res);
+      else
+        ok = lanczos_solve<double>(D, sp, tau, b, X, D.basis64, cnt, sc, &res);
+    } else {
+      ok = lanczos_solve<double>(D, sp, tau, b, X, D.basis64, cnt, sc, &res);
+    }
+  } else {
+    ok = gmres_solve<double>(D, sp, tau, b, X, D.basis64, cnt, sc, &res);
+  }
   if (ok && res > cnt.max_res) cnt.max_res = res;
   if (!ok) cnt.max_res = 1e300;
   return ok;
