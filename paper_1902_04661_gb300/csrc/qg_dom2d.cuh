@@ -76,7 +76,7 @@ struct Dom2D {
   // for alpha and for residual norms
   static constexpr bool kFusedDots = true;
   // the FP64 Lanczos solve keeps its vectors in the workspace basis (lanczos_stored_solve)
-  static constexpr bool kStoredLanczos = false;
+  static constexpr bool kStoredLanczos = true;
   const Inst2D* I;
   int len, N, n0, n1, S;
   int r_lo, r_hi, c_lo, c_hi;
