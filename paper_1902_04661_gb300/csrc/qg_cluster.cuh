@@ -198,6 +198,8 @@ struct DomC {
   static constexpr bool kFusedDots = false;
   // the FP64 Lanczos solve keeps its vectors in the workspace basis (lanczos_stored_solve)
   static constexpr bool kStoredLanczos = false;
+  // the same for the complex64 inner solves of the mixed form (the cluster form has no complex64 inner solve)
+  static constexpr bool kStoredLanczos32 = false;
   int len;        // S M local values per vector
   double dv;
   unsigned char* gm;

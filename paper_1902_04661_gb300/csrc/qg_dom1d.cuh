@@ -100,6 +100,8 @@ struct Dom1D {
   static constexpr bool kFusedDots = true;
   // the FP64 Lanczos solve keeps its vectors in the workspace basis (lanczos_stored_solve)
   static constexpr bool kStoredLanczos = true;
+  // the same for the complex64 inner solves of the mixed form (measured slower here: 82.3 against 79.9 ms per step of the mixed NaI-like batch)
+  static constexpr bool kStoredLanczos32 = false;
   int len;
   double2* su;    // staged U (shared memory) or null
   double dv;

@@ -77,6 +77,8 @@ struct Dom2D {
   static constexpr bool kFusedDots = true;
   // the FP64 Lanczos solve keeps its vectors in the workspace basis (lanczos_stored_solve)
   static constexpr bool kStoredLanczos = true;
+  // the same for the complex64 inner solves of the mixed form (measured faster here: 15.3 against 15.8 ms per 2-D mixed step)
+  static constexpr bool kStoredLanczos32 = true;
   const Inst2D* I;
   int len, N, n0, n1, S;
   int r_lo, r_hi, c_lo, c_hi;

@@ -534,11 +534,12 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
 // exact arithmetic the iterate of lanczos_solve, X_0 + V_k R^{-1} g.  Each
 // iteration then makes one vector pass besides H psi and its normalisation.
 // Needs a domain whose H psi forms the dots (kFusedDots) and m >= 2.
-template <class Dom>
-__device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, double tau, const double2* b, double2* X,
-                                     double2* basis, Counters& cnt, double* sc, double* res_out) {
-  using C = double2;
-  const GSmem<double> sm = gsmem<double>(D.gm, P.m);
+template <typename R, class Dom>
+__device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, R tau, const typename Cx<R>::T* b,
+                                     typename Cx<R>::T* X, typename Cx<R>::T* basis, Counters& cnt, R* sc,
+                                     double* res_out) {
+  using C = typename Cx<R>::T;
+  const GSmem<R> sm = gsmem<R>(D.gm, P.m);
   const int m = P.m;
   C* rr = sm.hess;            // R_jj
   C* rd = sm.hess + m;        // R_{j-1,j}
@@ -546,45 +547,45 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, double tau, c
   C* gv = sm.g;               // rotated right-hand side
   C* yv = sm.y;
   const int len = D.len;
-  const double dv = D.dv;
-  const C mic = make_double2(0.0, -tau);
-  double nv[1] = {0.0};
+  const R dv = (R)D.dv;
+  const C mic = cmk<C>((R)0, -tau);
+  R nv[1] = {(R)0};
   D.each([&](int i) {
     const C a = b[i];
     nv[0] = fma(a.x, a.x, fma(a.y, a.y, nv[0]));
   });
   if (!D.template sum<1>(nv, sc)) return false;
-  const double bn = sqrt(dv * sc[0]);
-  const double target = P.tol * bn;
+  const R bn = sqrt(dv * sc[0]);
+  const R target = (R)P.tol * bn;
   int total = 0;
   for (int guard = 0; guard < P.max_iters + 2; ++guard) {
     // V_0 = r / ||r||, r = b - A X  (= b on the first cycle when X starts at zero)
     C* V0 = basis;
-    double beta1;
+    R beta1;
     if (guard == 0 && P.x0_zero) {
       D.each([&](int i) { V0[i] = b[i]; });
       __syncthreads();
       beta1 = bn;
     } else {
-      D.template hpsi<double>(X, V0, b, 1.0, -1.0, mic, sc);
-      count_hpsi<double>(cnt);
+      D.template hpsi<R>(X, V0, b, (R)1, (R)-1, mic, sc);
+      count_hpsi<R>(cnt);
       if (!D.ok()) return false;
       beta1 = sqrt(dv * sc[1]);
     }
     if (guard > 0) cnt.restart++;
-    if (beta1 <= target || bn == 0.0) {
-      *res_out = (bn > 0.0) ? beta1 / bn : 0.0;
+    if (beta1 <= target || bn == (R)0) {
+      *res_out = (bn > (R)0) ? (double)(beta1 / bn) : 0.0;
       if (total > cnt.max_krylov) cnt.max_krylov = total;
       return true;
     }
     if (total >= P.max_iters) break;
-    const double ib = 1.0 / beta1;
+    const R ib = (R)1 / beta1;
     D.each([&](int i) { V0[i] = cscale(ib, V0[i]); });
     __syncthreads();
-    C g = make_double2(beta1, 0.0);
-    double c1 = 1.0, c2 = 1.0;
-    C s1 = make_double2(0.0, 0.0), s2 = make_double2(0.0, 0.0);
-    double betak = 0.0, res_est = beta1;
+    C g = cmk<C>(beta1, (R)0);
+    R c1 = (R)1, c2 = (R)1;
+    C s1 = cmk<C>((R)0, (R)0), s2 = cmk<C>((R)0, (R)0);
+    R betak = (R)0, res_est = beta1;
     bool conv = false;
     int nk = 0;   // columns of this cycle
     for (int k = 1; k <= m && total < P.max_iters; ++k) {
@@ -592,51 +593,51 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, double tau, c
       C* Wn = basis + (size_t)k * len;
       // Wn = H Vc - beta_k V_{k-2}; alpha reduced inside H psi
       if (k == 1)
-        D.template hpsi<double>(Vc, Wn, nullptr, 0.0, 0.0, make_double2(1.0, 0.0), sc);
+        D.template hpsi<R>(Vc, Wn, nullptr, (R)0, (R)0, cmk<C>((R)1, (R)0), sc);
       else
-        D.template hpsi<double>(Vc, Wn, basis + (size_t)(k - 2) * len, -betak, 0.0, make_double2(1.0, 0.0), sc);
-      count_hpsi<double>(cnt);
+        D.template hpsi<R>(Vc, Wn, basis + (size_t)(k - 2) * len, -betak, (R)0, cmk<C>((R)1, (R)0), sc);
+      count_hpsi<R>(cnt);
       if (!D.ok()) return false;
-      const double alpha = dv * sc[0];
-      double wv[1] = {0.0};
+      const R alpha = dv * sc[0];
+      R wv[1] = {(R)0};
       D.each([&](int i) {
         const C w = caxpy_r(-alpha, Vc[i], Wn[i]);
         Wn[i] = w;
         wv[0] = fma(w.x, w.x, fma(w.y, w.y, wv[0]));
       });
       if (!D.template sum<1>(wv, sc)) return false;
-      const double betan = sqrt(dv * sc[0]);
+      const R betan = sqrt(dv * sc[0]);
       // column k of [I; 0] + i tau T: rows k-1, k, k+1, rotated (as lanczos_solve)
-      C eps = make_double2(0.0, 0.0);
-      C del = make_double2(0.0, tau * betak);
-      C gam = make_double2(1.0, tau * alpha);
-      const C nu = make_double2(0.0, tau * betan);
+      C eps = cmk<C>((R)0, (R)0);
+      C del = cmk<C>((R)0, tau * betak);
+      C gam = cmk<C>((R)1, tau * alpha);
+      const C nu = cmk<C>((R)0, tau * betan);
       if (k >= 3) {
         eps = cmul(s2, del);
         del = cscale(c2, del);
       }
       if (k >= 2) {
         const C t = caxpy(s1, gam, cscale(c1, del));
-        gam = cnaxpy(make_double2(s1.x, -s1.y), del, cscale(c1, gam));
+        gam = cnaxpy(cmk<C>(s1.x, -s1.y), del, cscale(c1, gam));
         del = t;
       }
-      const double aa = hypot(gam.x, gam.y);
-      const double nn = hypot(nu.x, nu.y);
-      double c;
+      const R aa = hypot(gam.x, gam.y);
+      const R nn = hypot(nu.x, nu.y);
+      R c;
       C s, r;
-      if (nn == 0.0) {
-        c = 1.0;
-        s = make_double2(0.0, 0.0);
+      if (nn == (R)0) {
+        c = (R)1;
+        s = cmk<C>((R)0, (R)0);
         r = gam;
-      } else if (aa == 0.0) {
-        c = 0.0;
-        s = make_double2(nu.x / nn, -nu.y / nn);
-        r = make_double2(nn, 0.0);
+      } else if (aa == (R)0) {
+        c = (R)0;
+        s = cmk<C>(nu.x / nn, -nu.y / nn);
+        r = cmk<C>(nn, (R)0);
       } else {
-        const double rho = hypot(aa, nn);
-        const C ph = make_double2(gam.x / aa, gam.y / aa);
+        const R rho = hypot(aa, nn);
+        const C ph = cmk<C>(gam.x / aa, gam.y / aa);
         c = aa / rho;
-        s = cscale(1.0 / rho, cmul(ph, make_double2(nu.x, -nu.y)));
+        s = cscale((R)1 / rho, cmul(ph, cmk<C>(nu.x, -nu.y)));
         r = cscale(rho, ph);
       }
       if (threadIdx.x == 0) {
@@ -645,7 +646,7 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, double tau, c
         re[k - 1] = eps;
         gv[k - 1] = cscale(c, g);
       }
-      g = make_double2(-(s.x * g.x + s.y * g.y), -(s.x * g.y - s.y * g.x));   // -conj(s) g
+      g = cmk<C>(-(s.x * g.x + s.y * g.y), -(s.x * g.y - s.y * g.x));   // -conj(s) g
       res_est = hypot(g.x, g.y);
       nk = k;
       total++;
@@ -661,9 +662,9 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, double tau, c
         conv = true;
         break;
       }
-      if (betan <= 1e-300) break;
+      if (betan <= (sizeof(R) == 8 ? (R)1e-300 : (R)1e-35)) break;
       // V_k = Wn / beta_{k+1}, needed only by further iterations
-      const double ibn = 1.0 / betan;
+      const R ibn = (R)1 / betan;
       D.each([&](int i) { Wn[i] = cscale(ibn, Wn[i]); });
       __syncthreads();
     }
@@ -675,8 +676,8 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, double tau, c
         if (j + 1 < nk) t = cnaxpy(rd[j + 1], yv[j + 1], t);
         if (j + 2 < nk) t = cnaxpy(re[j + 2], yv[j + 2], t);
         const C q = rr[j];
-        const double iq = 1.0 / fma(q.x, q.x, q.y * q.y);
-        yv[j] = cmul(t, make_double2(q.x * iq, -q.y * iq));
+        const R iq = (R)1 / fma(q.x, q.x, q.y * q.y);
+        yv[j] = cmul(t, cmk<C>(q.x * iq, -q.y * iq));
       }
     }
     __syncthreads();
@@ -687,7 +688,7 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, double tau, c
     });
     __syncthreads();
     if (conv && !P.true_res) {
-      *res_out = (bn > 0.0) ? res_est / bn : 0.0;
+      *res_out = (bn > (R)0) ? (double)(res_est / bn) : 0.0;
       if (total > cnt.max_krylov) cnt.max_krylov = total;
       return true;
     }
@@ -715,7 +716,7 @@ __device__ bool solve_fp64(Dom& D, const StepPlan& P, double tau, const double2*
     ok = false;
     if constexpr (Dom::kStoredLanczos) {
       if (sp.m >= 2)
-        ok = lanczos_stored_solve(D, sp, tau, b, X, D.basis64, cnt, sc, &res);
+        ok = lanczos_stored_solve<double>(D, sp, tau, b, X, D.basis64, cnt, sc, &res);
       else
         ok = lanczos_solve<double>(D, sp, tau, b, X, D.basis64, cnt, sc, &res);
     } else {
@@ -818,9 +819,16 @@ __device__ bool solve_mixed(Dom& D, const StepPlan& P, double tau, const double2
     });
     __syncthreads();
     double res = 0.0;
-    if (P.solver == QG_SOLVER_LANCZOS)
-      lanczos_solve<float>(D, sp, (float)tau, r32, d32, D.basis32, cnt, scf, &res);
-    else
+    if (P.solver == QG_SOLVER_LANCZOS) {
+      if constexpr (Dom::kStoredLanczos32) {
+        if (sp.m >= 2)
+          lanczos_stored_solve<float>(D, sp, (float)tau, r32, d32, D.basis32, cnt, scf, &res);
+        else
+          lanczos_solve<float>(D, sp, (float)tau, r32, d32, D.basis32, cnt, scf, &res);
+      } else {
+        lanczos_solve<float>(D, sp, (float)tau, r32, d32, D.basis32, cnt, scf, &res);
+      }
+    } else
       gmres_solve<float>(D, sp, (float)tau, r32, d32, D.basis32, cnt, scf, &res);
     if (!D.ok()) return false;
     D.each([&](int i) {
