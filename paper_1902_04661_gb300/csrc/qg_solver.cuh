@@ -588,17 +588,27 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, R tau, const 
     R betak = (R)0, res_est = beta1;
     bool conv = false;
     int nk = 0;   // columns of this cycle
+    // The basis holds s_j = gam_j v_j, the Lanczos vectors times known
+    // scales, so no iteration needs a normalisation pass: with x = s_{k-1},
+    // H x - (gam_{k-1} beta_{k-1} / gam_{k-2}) s_{k-2} = gam_{k-1} (H v_{k-1}
+    // - beta_{k-1} v_{k-2}), alpha = Re<x, that> / gam_{k-1}^2, and the pass
+    // that removes alpha x leaves gam_{k-1} beta_k v_k = s_k.  A scale that
+    // leaves [lo, hi] is reset to 1 by one scaling pass.
+    const R lo = sizeof(R) == 8 ? (R)1e-100 : (R)1e-15, hi = (R)1 / lo;
+    R gprev = (R)1, gcur = (R)1;   // gam_{k-2}, gam_{k-1}
+    if (threadIdx.x == 0) sm.gc[0] = (R)1;
     for (int k = 1; k <= m && total < P.max_iters; ++k) {
       const C* Vc = basis + (size_t)(k - 1) * len;
       C* Wn = basis + (size_t)k * len;
-      // Wn = H Vc - beta_k V_{k-2}; alpha reduced inside H psi
+      // Wn = gam_{k-1} (H v_{k-1} - beta_{k-1} v_{k-2}); alpha reduced inside H psi
       if (k == 1)
         D.template hpsi<R>(Vc, Wn, nullptr, (R)0, (R)0, cmk<C>((R)1, (R)0), sc);
       else
-        D.template hpsi<R>(Vc, Wn, basis + (size_t)(k - 2) * len, -betak, (R)0, cmk<C>((R)1, (R)0), sc);
+        D.template hpsi<R>(Vc, Wn, basis + (size_t)(k - 2) * len, -(gcur * betak / gprev), (R)0,
+                           cmk<C>((R)1, (R)0), sc);
       count_hpsi<R>(cnt);
       if (!D.ok()) return false;
-      const R alpha = dv * sc[0];
+      const R alpha = dv * sc[0] / (gcur * gcur);
       R wv[1] = {(R)0};
       D.each([&](int i) {
         const C w = caxpy_r(-alpha, Vc[i], Wn[i]);
@@ -606,7 +616,7 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, R tau, const 
         wv[0] = fma(w.x, w.x, fma(w.y, w.y, wv[0]));
       });
       if (!D.template sum<1>(wv, sc)) return false;
-      const R betan = sqrt(dv * sc[0]);
+      const R betan = sqrt(dv * sc[0]) / gcur;
       // column k of [I; 0] + i tau T: rows k-1, k, k+1, rotated (as lanczos_solve)
       C eps = cmk<C>((R)0, (R)0);
       C del = cmk<C>((R)0, tau * betak);
@@ -663,12 +673,19 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, R tau, const 
         break;
       }
       if (betan <= (sizeof(R) == 8 ? (R)1e-300 : (R)1e-35)) break;
-      // V_k = Wn / beta_{k+1}, needed only by further iterations
-      const R ibn = (R)1 / betan;
-      D.each([&](int i) { Wn[i] = cscale(ibn, Wn[i]); });
-      __syncthreads();
+      // gam_k of s_k = Wn; rescaled to 1 when it leaves [lo, hi]
+      R gnew = gcur * betan;
+      if (!(gnew >= lo && gnew <= hi)) {
+        const R ig = (R)1 / gnew;
+        D.each([&](int i) { Wn[i] = cscale(ig, Wn[i]); });
+        __syncthreads();
+        gnew = (R)1;
+      }
+      gprev = gcur;
+      gcur = gnew;
+      if (threadIdx.x == 0 && k < m) sm.gc[k] = gnew;
     }
-    // y = R^{-1} g by back substitution, then X += V y
+    // y = R^{-1} g by back substitution, then X += V y = sum_j (y_j / gam_j) s_j
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int j = nk - 1; j >= 0; --j) {
@@ -679,6 +696,7 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, R tau, const 
         const R iq = (R)1 / fma(q.x, q.x, q.y * q.y);
         yv[j] = cmul(t, cmk<C>(q.x * iq, -q.y * iq));
       }
+      for (int j = 0; j < nk; ++j) yv[j] = cscale((R)1 / sm.gc[j], yv[j]);
     }
     __syncthreads();
     D.each([&](int i) {
