@@ -526,14 +526,15 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
 }
 
 // The same minimal-residual iteration with the Lanczos vectors kept: V_0..V_k
-// in basis (m + 1 slots, the GMRES basis of the workspace).  Instead of
-// updating two search directions and X in every iteration, X += V_k y once per
-// cycle, y solving R y = g with R the banded upper-triangular factor of
-// [I; 0] + i tau T_k that the Givens rotations build (diagonal r, then del and
-// eps one and two rows above it) and g the rotated right-hand side -- in
-// exact arithmetic the iterate of lanczos_solve, X_0 + V_k R^{-1} g.  Each
-// iteration then makes one vector pass besides H psi and its normalisation.
-// Needs a domain whose H psi forms the dots (kFusedDots) and m >= 2.
+// in basis (m + 1 slots, the GMRES basis of the workspace), each times a
+// tracked scale (see below).  Instead of updating two search directions and X
+// in every iteration, X += V_k y once per cycle, y solving R y = g with R the
+// banded upper-triangular factor of [I; 0] + i tau T_k that the Givens
+// rotations build (diagonal r, then del and eps one and two rows above it)
+// and g the rotated right-hand side -- in exact arithmetic the iterate of
+// lanczos_solve, X_0 + V_k R^{-1} g.  Each iteration then makes one vector
+// pass besides H psi.  Needs a domain whose H psi forms the dots (kFusedDots)
+// and m >= 2.
 template <typename R, class Dom>
 __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, R tau, const typename Cx<R>::T* b,
                                      typename Cx<R>::T* X, typename Cx<R>::T* basis, Counters& cnt, R* sc,
