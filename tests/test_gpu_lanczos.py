@@ -44,3 +44,52 @@ def test_lanczos_equals_gmres_full_size(qglib, cuda):
     assert err < 1e-11
     # one exact H psi per composed step (3), then 1 + I per sub-step
     assert lb["n_hpsi"] == 3 + lb["n_substeps"] + lb["n_krylov"] + lb["n_restart"]
+
+
+@pytest.mark.parametrize("restart,true_residual", [(2, 0), (3, 1)])
+def test_lanczos_short_cycles_vs_oracle(qglib, cuda, restart, true_residual):
+    """Cycles of two or three Lanczos columns: the FP64 solve forms its iterate
+    X += V y at the end of every cycle and restarts from the true residual
+    (Sec. II B's Krylov solve, restarted); the result must not depend on it."""
+    qmin, qmax, n = 3.8, 12.0, 128
+    grid, model = nai_library_model(qglib, n, qmin, qmax)
+    V, F = nai_oracle_fields(n, qmin, qmax)
+    H = oham.dense_h([qmin], [qmax], [n], [wl.NAI_REDUCED_MASS], V, F)
+    q, dq = ogrid.points(qmin, qmax, n)
+    psi0 = oinit.state_on_surface(2, 1, oinit.gaussian([q], [5.2], [4.0], [0.35]))
+    st = qglib.State(model)
+    st.set(psi0)
+    opts = qglib.default_solver_opts(tol=1e-14, restart=restart, max_iters=400, solver=qglib.QG_SOLVER_LANCZOS,
+                                     true_residual=true_residual)
+    s = st.propagate(1, 4, 1, 1.0 * FS, 2, opts)
+    want = oprop.DenseStepper(H).propagate(psi0, 1.0 * FS, 2, 1, 4, 1)
+    err = rel_l2(st.get(), want)
+    print("lanczos restart %d: %.2e, restarts %d" % (restart, err, s["n_restart"]))
+    assert s["n_restart"] > 0
+    assert err < 1e-11
+
+
+def test_lanczos_scale_safeguard_vs_oracle(qglib, cuda):
+    """H scaled by 1e40 (V times 1e40, mass divided by 1e40) and dt divided by
+    1e40 is the same evolution.  The Lanczos vectors grow by about |H| per
+    column, so their tracked scales leave [1e-100, 1e100] within three columns
+    and the solver's rescaling pass runs; the result must match the oracle."""
+    lam = 1e40
+    qmin, qmax, n = 3.8, 12.0, 128
+    V, F = nai_oracle_fields(n, qmin, qmax)
+    mass = wl.NAI_REDUCED_MASS / lam
+    g = qglib.Grid([n], [qmin], [qmax])
+    model = qglib.Model(g, 2, [mass], V=V * lam, F=F)
+    H = oham.dense_h([qmin], [qmax], [n], [mass], V * lam, F)
+    q, dq = ogrid.points(qmin, qmax, n)
+    psi0 = oinit.state_on_surface(2, 1, oinit.gaussian([q], [5.2], [4.0], [0.35]))
+    st = qglib.State(model)
+    st.set(psi0)
+    opts = qglib.default_solver_opts(tol=1e-14, solver=qglib.QG_SOLVER_LANCZOS)
+    dt = 1.0 * FS / lam
+    s = st.propagate(1, 4, 1, dt, 2, opts)
+    want = oprop.DenseStepper(H).propagate(psi0, dt, 2, 1, 4, 1)
+    err = rel_l2(st.get(), want)
+    print("lanczos with H x 1e40: %.2e, krylov/substep %.1f" % (err, s["n_krylov"] / s["n_substeps"]))
+    assert s["n_krylov"] >= 3 * s["n_substeps"]
+    assert err < 1e-11
