@@ -46,11 +46,12 @@ def test_lanczos_equals_gmres_full_size(qglib, cuda):
     assert lb["n_hpsi"] == 3 + lb["n_substeps"] + lb["n_krylov"] + lb["n_restart"]
 
 
-@pytest.mark.parametrize("restart,true_residual", [(2, 0), (3, 1)])
+@pytest.mark.parametrize("restart,true_residual", [(4, 0), (5, 1)])
 def test_lanczos_short_cycles_vs_oracle(qglib, cuda, restart, true_residual):
-    """Cycles of two or three Lanczos columns: the FP64 solve forms its iterate
-    X += V y at the end of every cycle and restarts from the true residual
-    (Sec. II B's Krylov solve, restarted); the result must not depend on it."""
+    """Cycles of four or five Lanczos columns (the shortest the library
+    accepts for this solver): the FP64 solve forms its iterate X += V y at the
+    end of every cycle and restarts from the true residual (Sec. II B's Krylov
+    solve, restarted); the result must not depend on it."""
     qmin, qmax, n = 3.8, 12.0, 128
     grid, model = nai_library_model(qglib, n, qmin, qmax)
     V, F = nai_oracle_fields(n, qmin, qmax)
