@@ -655,9 +655,9 @@ __device__ __forceinline__ R wcoupling(const R* __restrict__ F, int n, int S, in
 
 // y = e z + a x + c (H x) in the diabatic representation (Sec. II E):
 // H = -hbar^2/(2m) D^2 1 + W(q), two transforms per surface and the
-// pointwise symmetric W.  DOTS: also Re<x, y> and ||y||^2 (raw sums) in
+// pointwise symmetric W.  DOTS (bit 0, bit 1): also Re<x, y>, ||y||^2 (raw sums) in
 // dots[0..1].  y may alias x or z.
-template <typename R, bool DOTS>
+template <typename R, int DOTS>
 __device__ __noinline__ void apply_h_diabatic(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
                                                  const typename Cx<R>::T* x, typename Cx<R>::T* y,
                                                  const typename Cx<R>::T* z, R e, R a, typename Cx<R>::T c, R* red,
@@ -688,10 +688,8 @@ __device__ __noinline__ void apply_h_diabatic(const HOp<R>& H, typename Cx<R>::T
         C out = caxpy(c, acc, cmk<C>(a * xs.x, a * xs.y));
         if (e != (R)0) out = caxpy_r(e, z[s * n + j], out);
         y[s * n + j] = out;
-        if (DOTS) {
-          d[0] = fma(xs.x, out.x, fma(xs.y, out.y, d[0]));
-          d[1] = fma(out.x, out.x, fma(out.y, out.y, d[1]));
-        }
+        if (DOTS & 1) d[0] = fma(xs.x, out.x, fma(xs.y, out.y, d[0]));
+        if (DOTS & 2) d[1] = fma(out.x, out.x, fma(out.y, out.y, d[1]));
       } else {
         H.U[s * n + j] = acc;
       }
@@ -704,10 +702,8 @@ __device__ __noinline__ void apply_h_diabatic(const HOp<R>& H, typename Cx<R>::T
       C out = caxpy(c, H.U[i], cmk<C>(a * xs.x, a * xs.y));
       if (e != (R)0) out = caxpy_r(e, z[i], out);
       y[i] = out;
-      if (DOTS) {
-        d[0] = fma(xs.x, out.x, fma(xs.y, out.y, d[0]));
-        d[1] = fma(out.x, out.x, fma(out.y, out.y, d[1]));
-      }
+      if (DOTS & 1) d[0] = fma(xs.x, out.x, fma(xs.y, out.y, d[0]));
+      if (DOTS & 2) d[1] = fma(out.x, out.x, fma(out.y, out.y, d[1]));
     }
     __syncthreads();
   }
@@ -778,9 +774,9 @@ __device__ __noinline__ void apply_h_axpby(const HOp<R>& H, typename Cx<R>::T* s
 // and fewer passes: the first forward pass of each derivative reads its
 // input directly (x from global memory, U from sU), and when all surfaces fit
 // in one FFT batch the coupling pass leaves U in the FFT buffer for the second
-// derivative.  DOTS: also returns the raw sums Re<x, y> and ||y||^2 in
+// derivative.  DOTS (bit 0, bit 1): also the raw sums Re<x, y>, ||y||^2 in
 // dots[0..1] (one CTA reduction).  y may alias x or z.
-template <typename R, bool DOTS>
+template <typename R, int DOTS>
 __device__ __noinline__ void apply_h_staged(const HOp<R>& H, typename Cx<R>::T* sbuf, int nb_cap,
                                                typename Cx<R>::T* sU, const typename Cx<R>::T* x,
                                                typename Cx<R>::T* y, const typename Cx<R>::T* z, R e, R a,
@@ -862,10 +858,8 @@ __device__ __noinline__ void apply_h_staged(const HOp<R>& H, typename Cx<R>::T* 
           C out = plain ? hx : caxpy(c, hx, cmk<C>(a * xs[u].x, a * xs[u].y));
           if (e != (R)0) out = caxpy_r(e, zz[u], out);
           y[s0 * n + i] = out;
-          if (DOTS) {
-            d[0] = fma(xs[u].x, out.x, fma(xs[u].y, out.y, d[0]));
-            d[1] = fma(out.x, out.x, fma(out.y, out.y, d[1]));
-          }
+          if (DOTS & 1) d[0] = fma(xs[u].x, out.x, fma(xs[u].y, out.y, d[0]));
+          if (DOTS & 2) d[1] = fma(out.x, out.x, fma(out.y, out.y, d[1]));
         }
       }
     }

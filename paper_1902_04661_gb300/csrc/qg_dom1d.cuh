@@ -166,18 +166,19 @@ struct Dom1D {
         apply_h_axpby<float>(H32, reinterpret_cast<float2*>(fb), 2 * nb_cap, x, y, z, e, a, c);
     }
   }
-  // the same, also returning the raw sums Re<x, y> and ||y||^2 in dots[0..1]
-  template <typename R>
+  // the same, also returning the raw sums Re<x, y> (W bit 0) and ||y||^2
+  // (W bit 1) in dots[0..1]
+  template <typename R, int W = 3>
   __device__ __forceinline__ void hpsi(const typename Cx<R>::T* x, typename Cx<R>::T* y,
                                        const typename Cx<R>::T* z, R e, R a, typename Cx<R>::T c, R* dots) {
     using C = typename Cx<R>::T;
     R* rd = reinterpret_cast<R*>(red);
     if (su) {
       if constexpr (sizeof(R) == 8)
-        apply_h_staged<double, true>(H64, reinterpret_cast<double2*>(fb), nb_cap, su, x, y, z, e, a, c, rd, dots);
+        apply_h_staged<double, W>(H64, reinterpret_cast<double2*>(fb), nb_cap, su, x, y, z, e, a, c, rd, dots);
       else
-        apply_h_staged<float, true>(H32, reinterpret_cast<float2*>(fb), 2 * nb_cap, reinterpret_cast<float2*>(su), x,
-                                    y, z, e, a, c, rd, dots);
+        apply_h_staged<float, W>(H32, reinterpret_cast<float2*>(fb), 2 * nb_cap, reinterpret_cast<float2*>(su), x,
+                                 y, z, e, a, c, rd, dots);
       return;
     }
     hpsi<R>(x, y, z, e, a, c);

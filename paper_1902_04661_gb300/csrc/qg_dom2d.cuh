@@ -150,9 +150,15 @@ struct Dom2D {
   // With dots (shared memory, 2 values): also dots[0] = sum Re(conj(x) y)
   // and dots[1] = sum |y|^2 over the whole grid (without the grid weight),
   // reduced in the closing grid barrier; every CTA gets the same values.
+  // Both sums are formed whichever of them W (bit 0, bit 1) asks for.
+  template <typename R, int W = 3>
+  __device__ __forceinline__ void hpsi(const typename Cx<R>::T* x, typename Cx<R>::T* y, const typename Cx<R>::T* z,
+                                       R e, R a, typename Cx<R>::T c, R* dots = nullptr) {
+    hpsi_all<R>(x, y, z, e, a, c, dots);
+  }
   template <typename R>
-  __device__ __noinline__ void hpsi(const typename Cx<R>::T* x, typename Cx<R>::T* y, const typename Cx<R>::T* z, R e, R a,
-                       typename Cx<R>::T c, R* dots = nullptr) {
+  __device__ __noinline__ void hpsi_all(const typename Cx<R>::T* x, typename Cx<R>::T* y, const typename Cx<R>::T* z,
+                                        R e, R a, typename Cx<R>::T c, R* dots) {
     using C = typename Cx<R>::T;
     // members in registers: the stores below go through generic pointers
     // that could alias *this, which would force reloads from local memory

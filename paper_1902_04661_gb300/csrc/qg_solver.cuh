@@ -351,7 +351,7 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
       __syncthreads();
       beta1 = bn;
     } else if constexpr (Dom::kFusedDots) {
-      D.template hpsi<R>(X, Vc, b, (R)1, (R)-1, mic, sc);
+      D.template hpsi<R, 2>(X, Vc, b, (R)1, (R)-1, mic, sc);
       count_hpsi<R>(cnt);
       if (!D.ok()) return false;
       beta1 = sqrt(dv * sc[1]);
@@ -395,9 +395,9 @@ __device__ bool lanczos_solve(Dom& D, const SolveParams& P, R tau, const typenam
         // that shortcut cancels, and the normalisation error it leaves in
         // v_{k+1} grows from one iteration to the next on stiff problems.
         if (k == 1)
-          D.template hpsi<R>(Vc, Wn, nullptr, (R)0, (R)0, cmk<C>((R)1, (R)0), sc);
+          D.template hpsi<R, 1>(Vc, Wn, nullptr, (R)0, (R)0, cmk<C>((R)1, (R)0), sc);
         else
-          D.template hpsi<R>(Vc, Wn, Vp, -betak, (R)0, cmk<C>((R)1, (R)0), sc);
+          D.template hpsi<R, 1>(Vc, Wn, Vp, -betak, (R)0, cmk<C>((R)1, (R)0), sc);
         count_hpsi<R>(cnt);
         if (!D.ok()) return false;
         alpha = dv * sc[0];
@@ -568,7 +568,7 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, R tau, const 
       __syncthreads();
       beta1 = bn;
     } else {
-      D.template hpsi<R>(X, V0, b, (R)1, (R)-1, mic, sc);
+      D.template hpsi<R, 2>(X, V0, b, (R)1, (R)-1, mic, sc);
       count_hpsi<R>(cnt);
       if (!D.ok()) return false;
       beta1 = sqrt(dv * sc[1]);
@@ -603,9 +603,9 @@ __device__ bool lanczos_stored_solve(Dom& D, const SolveParams& P, R tau, const 
       C* Wn = basis + (size_t)k * len;
       // Wn = gam_{k-1} (H v_{k-1} - beta_{k-1} v_{k-2}); alpha reduced inside H psi
       if (k == 1)
-        D.template hpsi<R>(Vc, Wn, nullptr, (R)0, (R)0, cmk<C>((R)1, (R)0), sc);
+        D.template hpsi<R, 1>(Vc, Wn, nullptr, (R)0, (R)0, cmk<C>((R)1, (R)0), sc);
       else
-        D.template hpsi<R>(Vc, Wn, basis + (size_t)(k - 2) * len, -(gcur * betak / gprev), (R)0,
+        D.template hpsi<R, 1>(Vc, Wn, basis + (size_t)(k - 2) * len, -(gcur * betak / gprev), (R)0,
                            cmk<C>((R)1, (R)0), sc);
       count_hpsi<R>(cnt);
       if (!D.ok()) return false;
@@ -792,7 +792,7 @@ __device__ bool solve_mixed(Dom& D, const StepPlan& P, double tau, const double2
       if (!D.template sum<1>(rv, sc)) return false;
       rho = sqrt(dv * sc[0]);
     } else if constexpr (Dom::kFusedDots) {
-      D.template hpsi<double>(X, Rv, b, 1.0, -1.0, mic, sc);
+      D.template hpsi<double, 2>(X, Rv, b, 1.0, -1.0, mic, sc);
       cnt.hpsi++;
       if (!D.ok()) return false;
       rho = sqrt(dv * sc[1]);
